@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the Monte Carlo diagonalization hot path on one GB300.
+
+Workload (the 4x4 configuration the throughput metric is quoted on): 4x4
+periodic square cluster, t = 1, t' = -0.3, U = 8, N_up = N_dn = 7, Monte Carlo
+basis of 1e7 states (beta = 0.2, seed 0, AFM seed state).  One step = one pass
+of the whole hot path over that basis: device index build from the
+device-resident basis words, then 200 Lanczos steps (H~ v with fp32 vectors and
+fp64 coefficients, fused Krylov update, fp64 tridiagonal eigensolves).
+
+value   = H~ v connections processed per second (nnz_offdiag(H~) x 200 per
+          step, all ranks) with the basis already in HBM;
+e2e     = the same through the C ABI from host words: mcd_set_basis (copy in,
+          index) + mcd_lanczos_ground + E0 back to the host, every step;
+roofline: the H~ v pair of kernels, algorithmic bytes N_f (8 + 2 L s) per
+          application over their mean CUDA-event duration in the timed steps.
+
+--impl reference times the oracle (the CPU fp64 implementation that the tests
+check the kernels against) on a bounded sample of the same workload.
+Multi-GPU: the path is run as independent replicas, one per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H·v Gconnections/s; Lanczos iters/s vs plain FP64 path at |ΔE0|<1e-6"
+UNIT = "Gconnections/s"
+L2_BYTES = 129 * 2 ** 20
+FALLBACK_HBM = 6800.0
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy test)"
+    return FALLBACK_HBM, "fallback (recipe figure, no measured file)"
+
+
+# ---- clocks ---------------------------------------------------------------------
+CLOCK_Q = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, bus_id: str | None):
+        self.bus = (bus_id or "").lower()
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.25)
+
+    def stop(self) -> dict:
+        time.sleep(0.25)
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if self.bus:
+            mine = [r for r in rows if len(r) > 1 and self.bus.endswith(r[1].lower()[-12:])]
+            rows = mine or rows
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[2]))
+                mx.append(float(r[3]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[6:10]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- oracle (CPU) ----------------------------------------------------------------
+def oracle_sample(n_states: int):
+    """Oracle-built MC basis of the benchmark lattice (bounded size) + model."""
+    import numpy as np
+    from oracle import hamiltonian as H, sampler as S
+    from workloads import configs
+    w = configs.square16_u8()
+    B = S.sample_basis(w.n_sites, w.lat.t, w.U_sites, w.n_up, w.n_dn, n_states, w.beta,
+                       [w.seed_word()], seed=w.seed)
+    M = H.Model(w.n_sites, w.lat.t, w.eps, w.U_sites)
+    x = np.random.default_rng(0).standard_normal(len(B))
+    return B, M, x
+
+
+def oracle_apply(B, M, x):
+    """One oracle y = H~ x: enumerate every hop of every state with a sorted
+    search over the basis (oracle.hamiltonian.build), then multiply."""
+    from oracle import hamiltonian as H
+    P = H.build(M, B)
+    y = P.sparse() @ x
+    return P.nnz_offdiag(), y
+
+
+def cpu_baseline(seconds: float = 12.0, n_states: int = 1 << 17) -> dict:
+    B, M, x = oracle_sample(n_states)
+    t0 = time.perf_counter()
+    conns, reps = 0, 0
+    while True:
+        nnz, _ = oracle_apply(B, M, x)
+        conns += nnz
+        reps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": conns / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} oracle H~x applications (hop enumeration + sorted search + fp64 multiply) on an "
+                      f"oracle-sampled {len(B)}-state MC basis of the same 4x4 t-t' lattice (nnz {nnz}); "
+                      f"{dt:.1f} s; numpy single-threaded; host has {os.cpu_count()} cores"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    B, M, x = oracle_sample(1 << 15)
+    for _ in range(args.warmup):
+        oracle_apply(B, M, x)
+    t0 = time.perf_counter()
+    conns = 0
+    for _ in range(args.steps):
+        nnz, _ = oracle_apply(B, M, x)
+        conns += nnz
+    dt = time.perf_counter() - t0
+    value = conns / dt / 1e9
+    sample = (f"each step: one oracle H~x on an oracle-sampled {len(B)}-state MC basis of the 4x4 t-t' lattice "
+              f"(nnz {nnz}), fp64, numpy single-threaded")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: oracle Monte Carlo basis (no dataset)",
+        "config": workload_config(args, reference=True),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def workload_config(args, reference=False):
+    return {"workload": "square4x4_tp-0.3_U8_Nup7_Ndn7_mcbasis1e7_lanczos200_fp32",
+            "lattice": "4x4 periodic square, R1=(4,0) R2=(0,4), t=1, t'=-0.3", "U": 8.0, "n_up": 7, "n_dn": 7,
+            "n_f": args.n_f, "mc_beta": 0.2, "mc_seed": 0, "lanczos_steps": args.iters, "ncols": 1,
+            "vectors": "fp32 (fp64 coefficients and reductions)",
+            "l2": "working set (3 fp32 vectors + index) > 129 MB L2 each H*v; no flush",
+            "parallelism": f"replicas x{args.gpus}" if not reference else "cpu"}
+
+
+def traffic_for(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, or None if the
+    kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    ent = d.get(kernel_key)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2509_22975_gb300", "csrc", "hv.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return ent["bytes_per_launch"] if ent.get("hv_cu_sha") == h else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mcd", choices=["mcd", "reference"])
+    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--n-f", dest="n_f", type=int, default=10_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import paper_2509_22975_gb300 as pkg
+    from workloads import configs
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    w = configs.square16_u8()
+    ctx = pkg.Context(local)
+    ctx.mcd_set_hamiltonian(w.lat.t, w.eps, w.U, w.n_up, w.n_dn)
+    t0 = time.perf_counter()
+    ctx.mcd_build_basis(w.seed, args.n_f, w.beta, [w.seed_word()])
+    t_sample = time.perf_counter() - t0
+    words = ctx.mcd_get_basis()
+    n = len(words)
+    words_dev = torch.from_numpy(words.view(np.int64)).to(dev)
+    info = ctx.mcd_basis_info()
+    nnz = info["nnz_offdiag"]
+
+    def step():
+        ctx.mcd_set_basis_device(words_dev)
+        return ctx.mcd_lanczos_ground(args.iters, 0.0, 0, pkg.MCD_F32)
+
+    for _ in range(args.warmup):
+        r32 = step()
+    torch.cuda.synchronize()
+    ctx.mcd_set_option(pkg.MCD_OPT_KERNEL_TIMING, 1)
+    ctx.mcd_kernel_times(reset=True)
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        pass
+    clk = ClockSampler(bus)
+    l0 = ctx.mcd_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        r32 = step()
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    launches = ctx.mcd_launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    kms, kcnt = ctx.mcd_kernel_times(reset=True)
+    ctx.mcd_set_option(pkg.MCD_OPT_KERNEL_TIMING, 0)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    conns_per_step = nnz * r32["iters"]
+    value = world * conns_per_step / (ms * 1e-3) / 1e9
+
+    # roofline of the H~v pair (pass B: dn-major up-hop kernel, pass A: up-major dn-hop + diagonal)
+    tB = kms[0] / max(kcnt[0], 1)
+    tA = kms[1] / max(kcnt[1], 1)
+    tU = kms[2] / max(kcnt[2], 1)
+    alg_bytes = n * (8 + 2 * 1 * 4)
+    peak, peak_src = measured_peak()
+    achieved = alg_bytes / ((tA + tB) * 1e-3) / 1e9
+    tb, ta = traffic_for("hv_pass_B_square16_fp32_L1"), traffic_for("hv_pass_A_square16_fp32_L1")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tb + ta) if (tb is not None and ta is not None) else None,
+                "kernel": "H~v pair (hv_block_kernel pass B + pass A), one application",
+                "algorithmic_bytes": alg_bytes, "peak_source": peak_src,
+                "mean_ms": {"pass_B": tB, "pass_A": tA, "krylov_update": tU},
+                "share_of_step": {"pass_B": kms[0] / args.steps / ms, "pass_A": kms[1] / args.steps / ms,
+                                  "krylov_update": kms[2] / args.steps / ms}}
+
+    # end to end through the C ABI from host words
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.mcd_set_basis(words)
+        re2e = ctx.mcd_lanczos_ground(args.iters, 0.0, 0, pkg.MCD_F32)
+        _E0 = re2e["E0"]
+    e2e_s = (time.perf_counter() - h0) / args.e2e_steps
+    chunks = list(range(16, args.iters + 1, 16)) + ([args.iters] if args.iters % 16 else [])
+    d2h = sum(8 * (2 * m + 1) for m in chunks) + 8 + 4 + 16   # a/b read-backs, E0, checks, block counts
+    h2d = n * 8
+    e2e = {"value": world * conns_per_step / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
+           "path": "mcd_set_basis(host words) + mcd_lanczos_ground + E0 to host"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic: Monte Carlo basis sampled by the library",
+           "config": workload_config(args), "roofline": roofline, "e2e": e2e,
+           "gpu_launches": launches, "clocks": clocks,
+           "basis": {"n_states": n, "nnz_offdiag": nnz, "n_up_blocks": info["n_up_blocks"],
+                     "n_dn_blocks": info["n_dn_blocks"], "sampler_s": t_sample},
+           "E0_fp32": r32["E0"], "lanczos_iters_per_s_fp32": r32["iters"] / (ms * 1e-3)}
+
+    if not args.no_fp64:
+        # fp64 form and the plain fp64 path (global binary search kernel), same 200 steps
+        for algo, key in ((0, "fp64_blocked"), (1, "fp64_plain")):
+            ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, algo)
+            torch.cuda.synchronize()
+            a0 = time.perf_counter()
+            r64 = ctx.mcd_lanczos_ground(args.iters, 0.0, 0, pkg.MCD_F64)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - a0
+            out[f"lanczos_iters_per_s_{key}"] = r64["iters"] / dt
+            out[f"E0_{key}"] = r64["E0"]
+        ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, 0)
+        out["dE0_fp32_vs_plain_fp64"] = abs(out["E0_fp32"] - out["E0_fp64_plain"])
+        out["fp32_speedup_vs_plain_fp64"] = out["lanczos_iters_per_s_fp32"] / out["lanczos_iters_per_s_fp64_plain"]
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

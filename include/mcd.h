@@ -1,0 +1,165 @@
+/*
+ * mcd.h -- C ABI of the Monte Carlo diagonalization hot path on one GB300.
+ *
+ * The library applies the Hubbard Hamiltonian (Eq. (1) of arXiv 2509.22975,
+ * generalised to hoppings t_ij, on-site energies eps_i and repulsions U_i)
+ * projected onto a truncated basis F~ of Fock states (Sec. "Subspace of the
+ * ground state", the Eq. defining H~_mn = <x~_m|H|x~_n>), without storing the
+ * matrix (App. B), and runs the Lanczos ground-state recursion (App. B) on it.
+ *
+ * Conventions
+ *   - Fock state word: w = (up << n_sites) | dn, bit i of each half = site i
+ *     (App. D: |90> = |0101;1010>, spin up in the high half).  n_sites <= 32.
+ *   - Fermionic mode order: up modes 0..n-1, then down modes 0..n-1.  A hop
+ *     c^dag_{i s} c_{j s} has sign (-1)^(occupied same-spin sites strictly
+ *     between i and j).
+ *   - A basis is a strictly ascending array of words of one (N_up, N_dn)
+ *     sector, at most 2^31 - 1 states.
+ *   - Vectors over the basis are row-major [n_states][ld] blocks of ncols <= ld
+ *     columns, in basis order, on the device of the context.
+ *
+ * Ownership: the caller owns every pointer it passes; host arrays are copied
+ * in before the call returns; device arrays are only used during the call,
+ * on the context's stream.  The context owns its Hamiltonian, basis, index
+ * and Krylov workspace and frees them in mcd_destroy.
+ *
+ * Errors: every entry point returns an mcd_status; negative values are
+ * errors and leave the context usable; mcd_last_error() describes the last
+ * failure of that context.  Positive values are warnings.  No exceptions
+ * cross the ABI.  A context is not thread-safe: use one per host thread.
+ */
+#ifndef MCD_H
+#define MCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcd_ctx mcd_ctx;
+
+typedef enum {
+  MCD_OK = 0,
+  MCD_W_SHORT = 1,            /* sampler stopped with fewer states than asked */
+  MCD_E_INVALID = -1,         /* bad argument, unsorted/duplicate basis, ... */
+  MCD_E_SECTOR = -2,          /* word or seed outside the (N_up, N_dn) sector */
+  MCD_E_OOM = -3,             /* host or device allocation failed */
+  MCD_E_CUDA = -4,            /* a CUDA call failed (message in last_error) */
+  MCD_E_NOT_CONVERGED = -5,   /* Lanczos hit max_iter above tolerance */
+  MCD_E_BREAKDOWN = -6,       /* non-finite Lanczos coefficient */
+  MCD_E_TIMEOUT = -7,         /* reserved: bounded device wait expired */
+  MCD_E_STATE = -8,           /* call out of order (no Hamiltonian / basis) */
+  MCD_E_NODEVICE = -9         /* device work asked of a host-only context */
+} mcd_status;
+
+typedef enum { MCD_F64 = 0, MCD_F32 = 1 } mcd_dtype;
+
+/* Sampler flags (mcd_build_basis). */
+#define MCD_SAMPLE_NEW_ONLY 1   /* next starting points = new states only */
+
+/* Options (mcd_set_option). */
+#define MCD_OPT_HV_ALGO 1       /* 0 = two-layout block kernels (default),
+                                   1 = plain per-state global binary search   */
+#define MCD_OPT_KERNEL_TIMING 2 /* 1 = record CUDA events around H*v launches */
+#define MCD_OPT_SAMPLER_THREADS 3 /* host threads of the sampler (0 = auto)  */
+
+/* Create a context on CUDA device `device` using `cuda_stream` (a
+ * cudaStream_t, may be NULL for the legacy default stream).  device = -1
+ * makes a host-only context: Hamiltonian, sampler and basis calls work, every
+ * device call returns MCD_E_NODEVICE.  *out is NULL on failure. */
+int mcd_create(mcd_ctx** out, int device, void* cuda_stream);
+int mcd_destroy(mcd_ctx* ctx);
+int mcd_set_stream(mcd_ctx* ctx, void* cuda_stream);
+int mcd_set_option(mcd_ctx* ctx, int option, int64_t value);
+/* Message of the last failure of ctx ("" if none).  Valid until the next call
+ * on ctx.  ctx may be NULL (then a static message about creation). */
+const char* mcd_last_error(const mcd_ctx* ctx);
+const char* mcd_status_string(int status);
+
+/* Eq. (1): H = sum_{i!=j,s} t[i*n+j] c^dag_{is} c_{js} + sum_{i,s} eps[i] n_{is}
+ *            + sum_i U[i] n_{i,up} n_{i,dn}.
+ * t: host [n*n] real, must be symmetric (else MCD_E_INVALID), diagonal
+ * ignored.  eps: host [n] or NULL (zero; the paper's -mu goes here).
+ * U: host [U_len] with U_len = 1 (uniform) or n.  1 <= n <= 32,
+ * 0 <= n_up, n_dn <= n.  Replaces any previous Hamiltonian and drops the
+ * basis if the sector changes. */
+int mcd_set_hamiltonian(mcd_ctx* ctx, int n_sites, const double* t, const double* eps,
+                        const double* U, int U_len, int n_up, int n_dn);
+
+/* Sec. "Subspace of the ground state": grow F~ from the seed words by steps,
+ * proposing every hopping term of every starting state and accepting a
+ * proposed state b with probability min(exp(-beta sum_i U_i n_i,up n_i,dn(b)), 1).
+ * Random draws: SplitMix64, keyed by (seed, step, parent word, hop id);
+ * the full rule is in the design notes and is shared with the oracle.
+ * seed_states: host [n_seed] >= 1 words of the sector.  Stops at exactly
+ * n_target states (a final overshooting step keeps the new states of smallest
+ * SplitMix64 priority), or earlier if no new state appears for 64 steps
+ * (returns MCD_W_SHORT).  n_target must not exceed the sector size.  The basis
+ * replaces the current one and is indexed on the device (if any). *n_out =
+ * basis size. Runs on host threads (MCD_OPT_SAMPLER_THREADS). */
+int mcd_build_basis(mcd_ctx* ctx, uint64_t seed, int64_t n_target, double beta,
+                    const uint64_t* seed_states, int64_t n_seed, int flags, int64_t* n_out);
+
+/* Install a basis given as host words (strictly ascending, all in the sector;
+ * anything else is MCD_E_INVALID / MCD_E_SECTOR, nothing is sorted silently)
+ * and build its device index. n >= 1. */
+int mcd_set_basis(mcd_ctx* ctx, const uint64_t* host_words, int64_t n);
+/* Same as mcd_set_basis for words already in device memory (dev_words[n] on
+ * the context's device).  Order and sector are checked on the device; the
+ * words are copied (the caller keeps ownership). */
+int mcd_set_basis_device(mcd_ctx* ctx, const uint64_t* dev_words, int64_t n);
+/* Copy the basis to host_out[cap]; *n = basis size (also when cap is short). */
+int mcd_get_basis(const mcd_ctx* ctx, uint64_t* host_out, int64_t cap, int64_t* n);
+/* Sizes of the installed basis and its index; nnz_offdiag = number of nonzero
+ * off-diagonal entries of H~ (counted on the device; pass NULL to skip). */
+int mcd_basis_info(mcd_ctx* ctx, int64_t* n_states, int64_t* n_up_blocks,
+                   int64_t* n_dn_blocks, int64_t* nnz_offdiag);
+
+/* y = H~ x (App. B: targets outside F~ are discarded, i.e. the projected
+ * matrix is applied).  x, y: device, dtype MCD_F64 or MCD_F32, row-major
+ * [n_states][ld], ncols columns (1 <= ncols <= ld); x and y must not overlap.
+ * FP32 vectors use fp64 hopping and diagonal coefficients (each split into
+ * two floats) and accumulate each row in fp32. */
+int mcd_apply(mcd_ctx* ctx, const void* x, void* y, int ncols, int ld, int dtype);
+
+/* Diagonal <x~_k|H|x~_k> of H~ in fp64, written to device diag_dev[n_states]. */
+int mcd_diagonal(mcd_ctx* ctx, double* diag_dev);
+
+/* Off-diagonal entries of H~ as (row, col, value = t_ij * sign) triples in
+ * device arrays of capacity cap, grouped by row (order inside a row is not
+ * specified).  *nnz = total count; with rows_dev == NULL only counts. */
+int mcd_connections(mcd_ctx* ctx, int64_t* rows_dev, int64_t* cols_dev, double* vals_dev,
+                    int64_t cap, int64_t* nnz);
+
+/* App. B: Lanczos ground state of H~ from a SplitMix64 start vector keyed by
+ * `seed`, normalised form of the recursion (a_n, b_n as in App. B), Krylov
+ * vectors and H~ products in dtype, coefficients and the tridiagonal
+ * eigenproblem in fp64.  Stops when the residual estimate b_{m} |s_{m-1}|
+ * < tol * max(1, |E0|), on an invariant subspace (b < 1e-14 scale), or at
+ * max_iter (then MCD_E_NOT_CONVERGED unless tol <= 0, which asks for exactly
+ * max_iter steps).  psi_dev (nullable): device [n_states] of dtype; receives
+ * the normalised Ritz vector sum_n |n><n|Omega_eff> (change-of-basis Eq. of
+ * App. B) by a second pass that regenerates the Krylov vectors; *residual is
+ * then |H~ psi - E0 psi|, else the estimate.  E0, iters, residual: host. */
+int mcd_lanczos_ground(mcd_ctx* ctx, int max_iter, double tol, uint64_t seed, int dtype,
+                       double* E0, void* psi_dev, int* iters, double* residual);
+
+/* Lanczos coefficients of the last mcd_lanczos_ground: a[cap], b[cap]
+ * (b[0] = 0); *m = number of steps. Host arrays. */
+int mcd_lanczos_coeffs(const mcd_ctx* ctx, double* a, double* b, int cap, int* m);
+
+/* Timing of H*v launches recorded with MCD_OPT_KERNEL_TIMING since the last
+ * reset: total milliseconds and launch count per kernel class
+ * (0 = dn-major up-hop pass, 1 = up-major dn-hop + diagonal pass,
+ *  2 = Krylov update, 3 = plain kernel).  reset != 0 clears after reading. */
+int mcd_kernel_times(mcd_ctx* ctx, double* ms, int64_t* count, int n_classes, int reset);
+
+/* Number of kernels this context has launched since creation (all entry
+ * points); *n receives the count. */
+int mcd_launch_count(const mcd_ctx* ctx, int64_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCD_H */

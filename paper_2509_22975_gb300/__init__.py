@@ -1,0 +1,225 @@
+"""Python binding of libmcd (the C ABI in include/mcd.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels (or, for the basis sampler, its host threads).  Device vectors are
+torch tensors; the context runs on torch's current CUDA stream.  The library
+must have been built (``paper_2509_22975_gb300.build.build()``); importing an
+entry point without it raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from .build import LIB as LIB_PATH, build  # noqa: F401
+
+MCD_OK, MCD_W_SHORT = 0, 1
+MCD_F64, MCD_F32 = 0, 1
+MCD_SAMPLE_NEW_ONLY = 1
+MCD_OPT_HV_ALGO, MCD_OPT_KERNEL_TIMING, MCD_OPT_SAMPLER_THREADS = 1, 2, 3
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mcd.h")
+
+_lib = None
+c_i64p = ctypes.POINTER(ctypes.c_int64)
+c_dp = ctypes.POINTER(ctypes.c_double)
+c_u64p = ctypes.POINTER(ctypes.c_uint64)
+c_vp = ctypes.c_void_p
+
+_SIGS = {
+    "mcd_create": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, c_vp]),
+    "mcd_destroy": (ctypes.c_int, [c_vp]),
+    "mcd_set_stream": (ctypes.c_int, [c_vp, c_vp]),
+    "mcd_set_option": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int64]),
+    "mcd_last_error": (ctypes.c_char_p, [c_vp]),
+    "mcd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mcd_set_hamiltonian": (ctypes.c_int, [c_vp, ctypes.c_int, c_dp, c_dp, c_dp, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int]),
+    "mcd_build_basis": (ctypes.c_int, [c_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double, c_u64p,
+                                       ctypes.c_int64, ctypes.c_int, c_i64p]),
+    "mcd_set_basis": (ctypes.c_int, [c_vp, c_u64p, ctypes.c_int64]),
+    "mcd_set_basis_device": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64]),
+    "mcd_get_basis": (ctypes.c_int, [c_vp, c_u64p, ctypes.c_int64, c_i64p]),
+    "mcd_launch_count": (ctypes.c_int, [c_vp, c_i64p]),
+    "mcd_basis_info": (ctypes.c_int, [c_vp, c_i64p, c_i64p, c_i64p, c_i64p]),
+    "mcd_apply": (ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "mcd_diagonal": (ctypes.c_int, [c_vp, c_vp]),
+    "mcd_connections": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.c_int64, c_i64p]),
+    "mcd_lanczos_ground": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_int,
+                                          c_dp, c_vp, ctypes.POINTER(ctypes.c_int), c_dp]),
+    "mcd_lanczos_coeffs": (ctypes.c_int, [c_vp, c_dp, c_dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "mcd_kernel_times": (ctypes.c_int, [c_vp, c_dp, c_i64p, ctypes.c_int, ctypes.c_int]),
+}
+
+
+class MCDError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mcd status {status}: {msg}")
+        self.status = status
+
+
+def lib():
+    """The loaded libmcd.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libmcd.so is not built ({LIB_PATH}); call paper_2509_22975_gb300.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/mcd.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mcd_[a-z0-9_]+)\s*\(", text)))
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return MCD_F64
+    if t.dtype == torch.float32:
+        return MCD_F32
+    raise TypeError("vectors must be float32 or float64")
+
+
+class Context:
+    """An mcd_ctx.  device=-1 gives a host-only context (sampler, basis)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.L = lib()
+        self.device = device
+        h = c_vp()
+        if device >= 0 and stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        st = self.L.mcd_create(ctypes.byref(h), device, stream or None)
+        if st != MCD_OK:
+            raise MCDError(st, self.L.mcd_last_error(None).decode())
+        self.h = h
+
+    # -- helpers ---------------------------------------------------------------
+    def _check(self, st: int, ok=(MCD_OK,)) -> int:
+        if st not in ok:
+            raise MCDError(st, self.L.mcd_last_error(self.h).decode())
+        return st
+
+    def _sync_stream(self):
+        if self.device >= 0:
+            import torch
+            self.L.mcd_set_stream(self.h, torch.cuda.current_stream(self.device).cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mcd_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    # -- ABI mirror -------------------------------------------------------------
+    def mcd_set_option(self, option: int, value: int):
+        return self._check(self.L.mcd_set_option(self.h, option, value))
+
+    def mcd_set_hamiltonian(self, t, eps, U, n_up: int, n_dn: int):
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        n = t.shape[0]
+        e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
+        u = np.ascontiguousarray(np.atleast_1d(U), dtype=np.float64)
+        ep = e.ctypes.data_as(c_dp) if e is not None else None
+        return self._check(self.L.mcd_set_hamiltonian(self.h, n, t.ctypes.data_as(c_dp), ep,
+                                                      u.ctypes.data_as(c_dp), len(u), n_up, n_dn))
+
+    def mcd_build_basis(self, seed: int, n_target: int, beta: float, seed_states, flags: int = 0):
+        s = np.ascontiguousarray(np.atleast_1d(seed_states), dtype=np.uint64)
+        n = ctypes.c_int64(0)
+        st = self.L.mcd_build_basis(self.h, seed, n_target, beta, s.ctypes.data_as(c_u64p), len(s), flags,
+                                    ctypes.byref(n))
+        self._check(st, ok=(MCD_OK, MCD_W_SHORT))
+        return st, n.value
+
+    def mcd_set_basis(self, words):
+        w = np.ascontiguousarray(words, dtype=np.uint64)
+        return self._check(self.L.mcd_set_basis(self.h, w.ctypes.data_as(c_u64p), len(w)))
+
+    def mcd_set_basis_device(self, words):
+        """Install a basis held in a device uint64/int64 torch tensor."""
+        self._sync_stream()
+        return self._check(self.L.mcd_set_basis_device(self.h, _ptr(words), words.numel()))
+
+    def mcd_launch_count(self) -> int:
+        n = ctypes.c_int64(0)
+        self._check(self.L.mcd_launch_count(self.h, ctypes.byref(n)))
+        return n.value
+
+    def mcd_get_basis(self) -> np.ndarray:
+        n = ctypes.c_int64(0)
+        self._check(self.L.mcd_get_basis(self.h, None, 0, ctypes.byref(n)))
+        out = np.empty(n.value, dtype=np.uint64)
+        self._check(self.L.mcd_get_basis(self.h, out.ctypes.data_as(c_u64p), len(out), ctypes.byref(n)))
+        return out
+
+    def mcd_basis_info(self, nnz: bool = True) -> dict:
+        v = [ctypes.c_int64(0) for _ in range(4)]
+        self._sync_stream()
+        self._check(self.L.mcd_basis_info(self.h, *(ctypes.byref(x) for x in v[:3]),
+                                          ctypes.byref(v[3]) if nnz else None))
+        return {"n_states": v[0].value, "n_up_blocks": v[1].value, "n_dn_blocks": v[2].value,
+                "nnz_offdiag": v[3].value if nnz else None}
+
+    def mcd_apply(self, x, y, ncols: int | None = None, ld: int | None = None):
+        """y = H~ x for torch tensors [n] or [n, ld] on this device."""
+        if x.dim() == 1:
+            nc, l = 1, 1
+        else:
+            nc, l = x.shape[1], x.stride(0)
+        nc = nc if ncols is None else ncols
+        l = l if ld is None else ld
+        self._sync_stream()
+        return self._check(self.L.mcd_apply(self.h, _ptr(x), _ptr(y), nc, l, _dtype_code(x)))
+
+    def mcd_diagonal(self, out):
+        self._sync_stream()
+        return self._check(self.L.mcd_diagonal(self.h, _ptr(out)))
+
+    def mcd_connections(self, rows=None, cols=None, vals=None) -> int:
+        n = ctypes.c_int64(0)
+        cap = 0 if rows is None else rows.numel()
+        self._sync_stream()
+        self._check(self.L.mcd_connections(self.h, _ptr(rows) or None, _ptr(cols) or None,
+                                           _ptr(vals) or None, cap, ctypes.byref(n)))
+        return n.value
+
+    def mcd_lanczos_ground(self, max_iter: int, tol: float, seed: int, dtype: int, psi=None,
+                           allow_not_converged: bool = False) -> dict:
+        E0, res = ctypes.c_double(0), ctypes.c_double(0)
+        it = ctypes.c_int(0)
+        self._sync_stream()
+        st = self.L.mcd_lanczos_ground(self.h, max_iter, tol, seed, dtype, ctypes.byref(E0),
+                                       _ptr(psi) or None, ctypes.byref(it), ctypes.byref(res))
+        self._check(st, ok=(MCD_OK, -5) if allow_not_converged else (MCD_OK,))
+        return {"status": st, "E0": E0.value, "iters": it.value, "residual": res.value}
+
+    def mcd_lanczos_coeffs(self):
+        m = ctypes.c_int(0)
+        self._check(self.L.mcd_lanczos_coeffs(self.h, None, None, 0, ctypes.byref(m)))
+        a, b = np.zeros(m.value), np.zeros(m.value)
+        self._check(self.L.mcd_lanczos_coeffs(self.h, a.ctypes.data_as(c_dp), b.ctypes.data_as(c_dp),
+                                              m.value, ctypes.byref(m)))
+        return a, b
+
+    def mcd_kernel_times(self, reset: bool = False):
+        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_int64 * 4)()
+        self._check(self.L.mcd_kernel_times(self.h, ms, cnt, 4, int(reset)))
+        return list(ms), list(cnt)

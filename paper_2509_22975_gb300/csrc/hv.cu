@@ -1,0 +1,651 @@
+// y = H~ x without storing H~ (App. B: out-of-basis targets are discarded,
+// which is the projected matrix of the truncated basis).
+//
+// H = H_up + H_dn + D with D diagonal (Eq. (1)).  A down-spin hop keeps the
+// up word, an up-spin hop keeps the down word, so
+//   pass B (dn-major blocks, states sharing a dn word): y[perm k] = sum over
+//     up-spin hops of t_ij sign x[target]          (stores every row once)
+//   pass A (up-major blocks = basis order):           y[k] += D_k x[k] +
+//     sum over dn-spin hops of t_ij sign x[target]
+// Within a pass every hop target lies in the state's own block, whose minor
+// words a CTA stages in shared memory and binary-searches.  H~ is real
+// symmetric, so row k is gathered from the targets of the hops of state k
+// (pull form: no atomics, each row written by one thread group).
+//
+// Thread mapping: a group of G lanes per state; lane g owns columns
+// [g*VEC, g*VEC+VEC) of each row and evaluates bonds g, g+G, ...; found
+// targets are broadcast within the group by shuffles, then every lane
+// gathers its column chunk of the target row (coalesced 16-byte loads when
+// the rows are aligned).
+#include <cmath>
+
+#include "mcd_internal.h"
+
+namespace mcd {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct HvArgs {
+  const void* x;
+  void* y;
+  int ncols;
+  int ld;
+  Layout L;
+  int n_sites;
+  double* dot_partials;   // pass A, single column: per-CTA sum x[k] y[k]
+  unsigned int* ticket;
+  double* dot_out;
+};
+
+template <typename T, int VEC>
+struct Chunk;
+template <>
+struct Chunk<float, 4> {
+  static __device__ __forceinline__ void load(const float* p, int cvalid, float* v) {
+    if (cvalid >= 4) {
+      float4 q = __ldg(reinterpret_cast<const float4*>(p));
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] = c < cvalid ? __ldg(p + c) : 0.f;
+    }
+  }
+  static __device__ __forceinline__ void store(float* p, int cvalid, const float* v) {
+    if (cvalid >= 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < cvalid) p[c] = v[c];
+    }
+  }
+};
+template <>
+struct Chunk<double, 2> {
+  static __device__ __forceinline__ void load(const double* p, int cvalid, double* v) {
+    if (cvalid >= 2) {
+      double2 q = __ldg(reinterpret_cast<const double2*>(p));
+      v[0] = q.x; v[1] = q.y;
+    } else {
+      v[0] = cvalid > 0 ? __ldg(p) : 0.0;
+      v[1] = 0.0;
+    }
+  }
+  static __device__ __forceinline__ void store(double* p, int cvalid, const double* v) {
+    if (cvalid >= 2)
+      *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    else if (cvalid > 0)
+      p[0] = v[0];
+  }
+};
+template <typename T>
+struct Chunk1 {
+  static __device__ __forceinline__ void load(const T* p, int cvalid, T* v) { v[0] = cvalid > 0 ? __ldg(p) : T(0); }
+  static __device__ __forceinline__ void store(T* p, int cvalid, const T* v) { if (cvalid > 0) p[0] = v[0]; }
+};
+template <typename T, int VEC>
+using ChunkOf = typename std::conditional<VEC == 1, Chunk1<T>, Chunk<T, VEC>>::type;
+
+// Position of key in the sorted a[lo, hi), or -1.
+__device__ __forceinline__ int find_sorted(const uint32_t* a, int lo, int hi, uint32_t key) {
+  int len = hi - lo;
+  if (len <= 0) return -1;
+  const uint32_t* p = a + lo;
+  while (len > 1) {
+    const int half = len >> 1;
+    if (p[half] <= key) p += half;
+    len -= half;
+  }
+  return (*p == key) ? int(p - a) : -1;
+}
+
+// Diagonal <w|H|w> in fp64 (Eq. (1)): eps_i (n_up + n_dn) + U_i n_up n_dn.
+__device__ __forceinline__ double diag_f64(const HamParams& hp, uint32_t up, uint32_t dn) {
+  if (hp.uniform) return hp.dtab[__popc(up & dn)];
+  double d = 0.0;
+  for (int i = 0; i < hp.n_sites; ++i) {
+    const int u = (up >> i) & 1, v = (dn >> i) & 1;
+    d += hp.eps[i] * double(u + v) + hp.U[i] * double(u & v);
+  }
+  return d;
+}
+
+template <typename T>
+struct Acc;
+// fp32 vectors: coefficient = hi + lo (two floats), two accumulators.
+template <>
+struct Acc<float> {
+  float h, l;
+  __device__ __forceinline__ void zero() { h = 0.f; l = 0.f; }
+  __device__ __forceinline__ void fma(float ch, float cl, float x) {
+    h = fmaf(ch, x, h);
+    l = fmaf(cl, x, l);
+  }
+  __device__ __forceinline__ float value() const { return h + l; }
+};
+template <>
+struct Acc<double> {
+  double h;
+  __device__ __forceinline__ void zero() { h = 0.0; }
+  __device__ __forceinline__ void fma(double c, double, double x) { h = ::fma(c, x, h); }
+  __device__ __forceinline__ double value() const { return h; }
+};
+
+template <typename T>
+struct Coef {
+  T hi, lo;
+};
+
+template <typename T>
+__device__ __forceinline__ Coef<T> bond_coef(const float* thi, const float* tlo, const double* t64, int b,
+                                             int sign);
+template <>
+__device__ __forceinline__ Coef<float> bond_coef<float>(const float* thi, const float* tlo, const double*, int b,
+                                                        int sign) {
+  return Coef<float>{sign ? -thi[b] : thi[b], sign ? -tlo[b] : tlo[b]};
+}
+template <>
+__device__ __forceinline__ Coef<double> bond_coef<double>(const float*, const float*, const double* t64, int b,
+                                                          int sign) {
+  return Coef<double>{sign ? -t64[b] : t64[b], 0.0};
+}
+
+template <typename T>
+__device__ __forceinline__ Coef<T> diag_coef(const HamParams& hp, uint32_t up, uint32_t dn);
+template <>
+__device__ __forceinline__ Coef<float> diag_coef<float>(const HamParams& hp, uint32_t up, uint32_t dn) {
+  if (hp.uniform) {
+    const int k = __popc(up & dn);
+    return Coef<float>{hp.dtab_hi[k], hp.dtab_lo[k]};
+  }
+  const double d = diag_f64(hp, up, dn);
+  const float h = float(d);
+  return Coef<float>{h, float(d - double(h))};
+}
+template <>
+__device__ __forceinline__ Coef<double> diag_coef<double>(const HamParams& hp, uint32_t up, uint32_t dn) {
+  return Coef<double>{diag_f64(hp, up, dn), 0.0};
+}
+
+// ---------------------------------------------------------------------------------
+template <typename T, int VEC, int G, bool PASS_A, bool DOT>
+__global__ void __launch_bounds__(kThreads) hv_block_kernel(const HvArgs a, const HamParams hp) {
+  extern __shared__ uint32_t s_minor[];
+  __shared__ uint32_t s_off[kItem + 2];
+  __shared__ uint32_t s_major[kItem + 1];
+  __shared__ uint32_t s_mask[kMaxBonds], s_betw[kMaxBonds];
+  __shared__ float s_thi[kMaxBonds], s_tlo[kMaxBonds];
+  __shared__ double s_t64[kMaxBonds];
+  __shared__ int s_nb, s_st0, s_staged;
+  __shared__ double s_red[kThreads / 32];
+
+  const Layout& L = a.L;
+  const int item = blockIdx.x;
+  const int64_t k0 = int64_t(item) * kItem;
+  const int64_t k1 = (k0 + kItem < L.n ? k0 + kItem : L.n);
+  const int nbonds = hp.n_bonds;
+  for (int b = threadIdx.x; b < nbonds; b += kThreads) {
+    s_mask[b] = hp.bonds[b].mask;
+    s_betw[b] = hp.bonds[b].between;
+    s_thi[b] = hp.bonds[b].t_hi;
+    s_tlo[b] = hp.bonds[b].t_lo;
+    s_t64[b] = hp.bonds[b].t;
+  }
+  if (threadIdx.x == 0) {
+    const uint32_t b0 = L.item_blk[item];
+    uint32_t b1 = L.item_blk[item + 1];
+    if (b1 == uint32_t(L.nblk) || L.blk_off[b1] == uint32_t(k1)) b1 -= 1;
+    s_nb = int(b1 - b0 + 1);
+    s_st0 = int(L.blk_off[b0]);
+    const int st1 = int(L.blk_off[b1 + 1]);
+    s_staged = (st1 - s_st0) <= kStageWords;
+  }
+  __syncthreads();
+  const int nb = s_nb, st0 = s_st0;
+  const uint32_t b0 = L.item_blk[item];
+  for (int j = threadIdx.x; j <= nb; j += kThreads) {
+    s_off[j] = L.blk_off[b0 + j];
+    if (j < nb) s_major[j] = L.blk_major[b0 + j];
+  }
+  __syncthreads();
+  const int st1 = int(s_off[nb]);
+  const uint32_t* mw;
+  int mbase;   // mw[pos - mbase] = minor word of layout position pos
+  if (s_staged) {
+    for (int p = threadIdx.x; p < st1 - st0; p += kThreads) s_minor[p] = L.minor[st0 + p];
+    mw = s_minor;
+    mbase = st0;
+    __syncthreads();
+  } else {
+    mw = L.minor + st0;
+    mbase = st0;
+  }
+
+  const T* __restrict__ x = static_cast<const T*>(a.x);
+  T* __restrict__ y = static_cast<T*>(a.y);
+  const int lane = threadIdx.x & 31;
+  const int g = lane % G;
+  const int group = threadIdx.x / G;
+  constexpr int kGroups = kThreads / G;
+  const unsigned gmask = 0xffffffffu;   // every lane runs the same trip counts
+  const int ncols = a.ncols, ld = a.ld;
+  const int ctile = G * VEC;
+  using C = ChunkOf<T, VEC>;
+  double dot_acc = 0.0;
+
+  // every group runs the same number of rounds so that shuffles stay uniform
+  const int rounds = (kItem + kGroups - 1) / kGroups;
+  for (int r = 0; r < rounds; ++r) {
+    const int64_t k = k0 + int64_t(r) * kGroups + group;
+    const bool live = k < k1;
+    // block of state k among the staged blocks
+    int j = 0;
+    if (live) {
+      int lo = 0, len = nb;
+      while (len > 1) {
+        const int half = len >> 1;
+        if (s_off[lo + half] <= uint32_t(k)) lo += half;
+        len -= half;
+      }
+      j = lo;
+    }
+    const int bbase = live ? int(s_off[j]) : 0;
+    const int bend = live ? int(s_off[j + 1]) : 0;
+    const uint32_t major = live ? s_major[j] : 0u;
+    const uint32_t m = live ? mw[k - mbase] : 0u;
+    const int64_t out_row = live ? (PASS_A ? k : int64_t(L.perm[k])) : 0;
+
+    for (int c0 = 0; c0 < ncols; c0 += ctile) {
+      const int col = c0 + g * VEC;
+      const int cvalid = ncols - col;
+      Acc<T> acc[VEC];
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) acc[c].zero();
+      for (int bb = 0; bb < nbonds; bb += G) {
+        const int b = bb + g;
+        int row = -1;
+        Coef<T> cf{T(0), T(0)};
+        if (live && b < nbonds) {
+          const uint32_t mk = s_mask[b];
+          if (__popc(m & mk) == 1) {
+            const uint32_t m2 = m ^ mk;
+            const int q = find_sorted(mw, bbase - mbase, bend - mbase, m2);
+            if (q >= 0) {
+              const int pos = q + mbase;
+              row = PASS_A ? pos : int(L.perm[pos]);
+              cf = bond_coef<T>(s_thi, s_tlo, s_t64, b, __popc(m & s_betw[b]) & 1);
+            }
+          }
+        }
+        if (G == 1) {
+          if (row >= 0 && cvalid > 0) {
+            T xv[VEC];
+            C::load(x + int64_t(row) * ld + col, cvalid, xv);
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) acc[c].fma(cf.hi, cf.lo, xv[c]);
+          }
+        } else {
+#pragma unroll
+          for (int s = 0; s < G; ++s) {
+            const int rr = __shfl_sync(gmask, row, s, G);
+            const T ch = __shfl_sync(gmask, cf.hi, s, G);
+            const T cl = __shfl_sync(gmask, cf.lo, s, G);
+            if (rr >= 0 && cvalid > 0) {
+              T xv[VEC];
+              C::load(x + int64_t(rr) * ld + col, cvalid, xv);
+#pragma unroll
+              for (int c = 0; c < VEC; ++c) acc[c].fma(ch, cl, xv[c]);
+            }
+          }
+        }
+      }
+      if (live && cvalid > 0) {
+        T out[VEC];
+        if (PASS_A) {
+          const Coef<T> dc = diag_coef<T>(hp, major, m);
+          T xv[VEC], yv[VEC];
+          C::load(x + k * ld + col, cvalid, xv);
+          C::load(y + k * ld + col, cvalid, yv);
+#pragma unroll
+          for (int c = 0; c < VEC; ++c) {
+            acc[c].fma(dc.hi, dc.lo, xv[c]);
+            out[c] = acc[c].value() + yv[c];
+          }
+          if (DOT) dot_acc += double(xv[0]) * double(out[0]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < VEC; ++c) out[c] = acc[c].value();
+        }
+        C::store(y + out_row * ld + col, cvalid, out);
+      }
+    }
+  }
+
+  if (DOT) {
+    // per-CTA partial of sum_k x[k] y[k]; the last CTA to finish sums the
+    // partials in a fixed order (deterministic) into *dot_out.
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot_acc += __shfl_xor_sync(0xffffffffu, dot_acc, o);
+    if (lane == 0) s_red[threadIdx.x >> 5] = dot_acc;
+    __syncthreads();
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) s += s_red[w];
+      a.dot_partials[blockIdx.x] = s;
+      __threadfence();
+      const unsigned t = atomicAdd(a.ticket, 1u);
+      s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+      double s = 0.0;
+      for (int i = threadIdx.x; i < int(gridDim.x); i += kThreads) s += __ldcg(a.dot_partials + i);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) s_red[threadIdx.x >> 5] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) tot += s_red[w];
+        *a.dot_out = tot;
+        *a.ticket = 0u;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Plain path: one thread per state, both spins, binary search over the whole
+// sorted basis in global memory.  Kept as the simple reference GPU path.
+template <typename T>
+__global__ void hv_plain_kernel(const uint64_t* __restrict__ words, int64_t n, const T* __restrict__ x,
+                                T* __restrict__ y, int ncols, int ld, const HamParams hp) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int ns = hp.n_sites;
+  const uint64_t w = words[k];
+  const uint64_t half = ns == 32 ? 0xFFFFFFFFull : ((1ull << ns) - 1);
+  const uint32_t up = uint32_t(w >> ns), dn = uint32_t(w & half);
+  const double d = diag_f64(hp, up, dn);
+  for (int c = 0; c < ncols; ++c) {
+    double acc = d * double(x[k * ld + c]);
+    for (int spin = 0; spin < 2; ++spin) {
+      const uint32_t ws = spin == 0 ? up : dn;
+      const int shift = spin == 0 ? ns : 0;
+      for (int b = 0; b < hp.n_bonds; ++b) {
+        const uint32_t mk = hp.bonds[b].mask;
+        if (__popc(ws & mk) != 1) continue;
+        const uint64_t w2 = w ^ (uint64_t(mk) << shift);
+        int64_t lo = 0, len = n;
+        while (len > 1) {
+          const int64_t h = len >> 1;
+          if (words[lo + h] <= w2) lo += h;
+          len -= h;
+        }
+        if (words[lo] != w2) continue;
+        const double t = (__popc(ws & hp.bonds[b].between) & 1) ? -hp.bonds[b].t : hp.bonds[b].t;
+        acc += t * double(x[lo * ld + c]);
+      }
+    }
+    y[k * ld + c] = T(acc);
+  }
+}
+
+__global__ void diag_kernel(const uint64_t* __restrict__ words, int64_t n, double* out, const HamParams hp) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int ns = hp.n_sites;
+  const uint64_t w = words[k];
+  const uint64_t half = ns == 32 ? 0xFFFFFFFFull : ((1ull << ns) - 1);
+  out[k] = diag_f64(hp, uint32_t(w >> ns), uint32_t(w & half));
+}
+
+// Connection dump, same hop enumeration, sign and in-block search as the
+// block kernels, one thread per state of a layout.  mode 0: cnt[row] +=
+// connections of this pass; mode 1: write triples at off[row] + (mode-1 base).
+template <bool PASS_A>
+__global__ void conn_kernel(const Layout L, const HamParams hp, uint32_t* cnt, const uint64_t* off,
+                            const uint32_t* cnt_first, int64_t* rows, int64_t* cols, double* vals, int write) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= L.n) return;
+  // block of k: binary search over blk_off
+  int64_t lo = 0, len = L.nblk;
+  while (len > 1) {
+    const int64_t h = len >> 1;
+    if (L.blk_off[lo + h] <= uint32_t(k)) lo += h;
+    len -= h;
+  }
+  const int bbase = int(L.blk_off[lo]), bend = int(L.blk_off[lo + 1]);
+  const uint32_t m = L.minor[k];
+  const int64_t row = PASS_A ? k : int64_t(L.perm[k]);
+  int64_t w = 0;
+  if (write) w = int64_t(off[row]) + (PASS_A ? int64_t(cnt_first[row]) : 0);
+  uint32_t c = 0;
+  for (int b = 0; b < hp.n_bonds; ++b) {
+    const uint32_t mk = hp.bonds[b].mask;
+    if (__popc(m & mk) != 1) continue;
+    const int q = find_sorted(L.minor, bbase, bend, m ^ mk);
+    if (q < 0) continue;
+    if (write) {
+      rows[w] = row;
+      cols[w] = PASS_A ? int64_t(q) : int64_t(L.perm[q]);
+      vals[w] = (__popc(m & hp.bonds[b].between) & 1) ? -hp.bonds[b].t : hp.bonds[b].t;
+      ++w;
+    }
+    ++c;
+  }
+  if (!write) cnt[row] = c;
+}
+
+__global__ void sum_counts_kernel(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* out,
+                                  uint64_t* excl /*nullable*/) {
+  // single-block running sum (n is at most ~1e8 and this runs once per basis)
+  __shared__ unsigned long long s_part[1024];
+  const int t = threadIdx.x;
+  const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t lo = t * chunk, hi = (lo + chunk < n ? lo + chunk : n);
+  unsigned long long s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += uint64_t(a[i]) + uint64_t(b[i]);
+  s_part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    unsigned long long run = 0;
+    for (int i = 0; i < int(blockDim.x); ++i) {
+      const unsigned long long v = s_part[i];
+      s_part[i] = run;
+      run += v;
+    }
+    *out = run;
+  }
+  __syncthreads();
+  if (excl) {
+    unsigned long long run = s_part[t];
+    for (int64_t i = lo; i < hi; ++i) {
+      excl[i] = run;
+      run += uint64_t(a[i]) + uint64_t(b[i]);
+    }
+  }
+}
+
+int grid_of(int64_t n, int t) { return int((n + t - 1) / t); }
+
+template <typename T, int VEC, int G>
+cudaError_t launch_pair(mcd_ctx* c, const void* x, void* y, int ncols, int ld, double* partials,
+                        unsigned int* ticket, double* dot_out) {
+  HvArgs a;
+  a.x = x;
+  a.y = y;
+  a.ncols = ncols;
+  a.ld = ld;
+  a.n_sites = c->n;
+  a.dot_partials = partials;
+  a.ticket = ticket;
+  a.dot_out = dot_out;
+  const size_t smem = kStageWords * sizeof(uint32_t);
+  static bool configured = false;   // per instantiation
+  if (!configured) {
+    cudaFuncSetAttribute(hv_block_kernel<T, VEC, G, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(hv_block_kernel<T, VEC, G, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(hv_block_kernel<T, VEC, G, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    configured = true;
+  }
+  a.L = c->idx.B;
+  timing_begin(c, 0);
+  hv_block_kernel<T, VEC, G, false, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+  MCD_LAUNCHED(c);
+  timing_end(c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  a.L = c->idx.A;
+  timing_begin(c, 1);
+  if (partials)
+    hv_block_kernel<T, VEC, G, true, true><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+  else
+    hv_block_kernel<T, VEC, G, true, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+  MCD_LAUNCHED(c);
+  timing_end(c);
+  return cudaGetLastError();
+}
+
+template <typename T, int VEC>
+cudaError_t dispatch_g(mcd_ctx* c, const void* x, void* y, int ncols, int ld, double* partials,
+                       unsigned int* ticket, double* dot_out) {
+  const int chunks = (ncols + VEC - 1) / VEC;
+  if (chunks <= 1) return launch_pair<T, VEC, 1>(c, x, y, ncols, ld, partials, ticket, dot_out);
+  if (chunks <= 2) return launch_pair<T, VEC, 2>(c, x, y, ncols, ld, partials, ticket, dot_out);
+  if (chunks <= 4) return launch_pair<T, VEC, 4>(c, x, y, ncols, ld, partials, ticket, dot_out);
+  if (chunks <= 8) return launch_pair<T, VEC, 8>(c, x, y, ncols, ld, partials, ticket, dot_out);
+  if (chunks <= 16) return launch_pair<T, VEC, 16>(c, x, y, ncols, ld, partials, ticket, dot_out);
+  return launch_pair<T, VEC, 32>(c, x, y, ncols, ld, partials, ticket, dot_out);
+}
+
+}  // namespace
+
+// ---- timing ---------------------------------------------------------------------
+void timing_begin(mcd_ctx* c, int cls) {
+  if (!c->timing || !c->tm) return;
+  Timing& t = *c->tm;
+  if (t.n_ev >= 1024) timing_collect(c);
+  const int i = t.n_ev;
+  t.cls[i] = cls;
+  cudaEventRecord(t.ev[2 * i], c->stream);
+}
+void timing_end(mcd_ctx* c) {
+  if (!c->timing || !c->tm) return;
+  Timing& t = *c->tm;
+  cudaEventRecord(t.ev[2 * t.n_ev + 1], c->stream);
+  ++t.n_ev;
+}
+void timing_collect(mcd_ctx* c) {
+  if (!c->tm) return;
+  Timing& t = *c->tm;
+  if (t.n_ev == 0) return;
+  cudaEventSynchronize(t.ev[2 * t.n_ev - 1]);
+  for (int i = 0; i < t.n_ev; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.ev[2 * i], t.ev[2 * i + 1]) == cudaSuccess) {
+      t.ms[t.cls[i]] += ms;
+      t.count[t.cls[i]] += 1;
+    }
+  }
+  t.n_ev = 0;
+}
+
+int hv_dot_ctas(mcd_ctx* c, int, int) { return int(c->idx.A.n_items); }
+
+int hv_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, double* dot_partials,
+             int dot_slot) {
+  (void)dot_slot;
+  cudaError_t e = cudaSuccess;
+  if (c->hv_algo == 1) {
+    const int T = 256;
+    timing_begin(c, 3);
+    if (dtype == MCD_F64)
+      hv_plain_kernel<double><<<grid_of(c->idx.n, T), T, 0, c->stream>>>(
+          c->idx.words, c->idx.n, static_cast<const double*>(x), static_cast<double*>(y), ncols, ld, *c->hp);
+    else
+      hv_plain_kernel<float><<<grid_of(c->idx.n, T), T, 0, c->stream>>>(
+          c->idx.words, c->idx.n, static_cast<const float*>(x), static_cast<float*>(y), ncols, ld, *c->hp);
+    MCD_LAUNCHED(c);
+    timing_end(c);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? MCD_OK : cuda_fail(c, e, "plain H*v launch");
+  }
+  unsigned int* ticket = nullptr;
+  double* dot_out = nullptr;
+  if (dot_partials) {
+    ticket = c->lw.ticket;
+    dot_out = c->lw.scal + dot_slot;
+  }
+  const bool vec_ok = [&] {
+    const size_t es = dtype == MCD_F64 ? 8 : 4;
+    const int vec = dtype == MCD_F64 ? 2 : 4;
+    return ncols > 1 && ld % vec == 0 && (reinterpret_cast<uintptr_t>(x) % 16 == 0) &&
+           (reinterpret_cast<uintptr_t>(y) % 16 == 0) && es > 0;
+  }();
+  if (dtype == MCD_F64) {
+    e = vec_ok ? dispatch_g<double, 2>(c, x, y, ncols, ld, dot_partials, ticket, dot_out)
+               : dispatch_g<double, 1>(c, x, y, ncols, ld, dot_partials, ticket, dot_out);
+  } else {
+    e = vec_ok ? dispatch_g<float, 4>(c, x, y, ncols, ld, dot_partials, ticket, dot_out)
+               : dispatch_g<float, 1>(c, x, y, ncols, ld, dot_partials, ticket, dot_out);
+  }
+  return e == cudaSuccess ? MCD_OK : cuda_fail(c, e, "H*v launch");
+}
+
+int hv_diagonal(mcd_ctx* c, double* out) {
+  const int T = 256;
+  diag_kernel<<<grid_of(c->idx.n, T), T, 0, c->stream>>>(c->idx.words, c->idx.n, out, *c->hp);
+  MCD_LAUNCHED(c);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? MCD_OK : cuda_fail(c, e, "diagonal");
+}
+
+int hv_connections(mcd_ctx* c, int64_t* rows, int64_t* cols, double* vals, int64_t cap, int64_t* nnz) {
+  const int64_t n = c->idx.n;
+  const int T = 256;
+  cudaStream_t s = c->stream;
+  uint32_t *ca = nullptr, *cb = nullptr;
+  uint64_t* off = nullptr;
+  unsigned long long* tot = nullptr;
+  cudaError_t e = cudaMallocAsync(&ca, n * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&cb, n * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&off, n * 8, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&tot, 8, s);
+  unsigned long long htot = 0;
+  if (e == cudaSuccess) {
+    conn_kernel<false><<<grid_of(n, T), T, 0, s>>>(c->idx.B, *c->hp, cb, nullptr, nullptr, nullptr, nullptr,
+                                                   nullptr, 0);
+    MCD_LAUNCHED(c);
+    conn_kernel<true><<<grid_of(n, T), T, 0, s>>>(c->idx.A, *c->hp, ca, nullptr, nullptr, nullptr, nullptr,
+                                                  nullptr, 0);
+    MCD_LAUNCHED(c);
+    sum_counts_kernel<<<1, 1024, 0, s>>>(cb, ca, n, tot, rows ? off : nullptr);
+    MCD_LAUNCHED(c);
+    e = cudaMemcpyAsync(&htot, tot, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e == cudaSuccess && rows) {
+    if (int64_t(htot) > cap) {
+      cudaFreeAsync(ca, s); cudaFreeAsync(cb, s); cudaFreeAsync(off, s); cudaFreeAsync(tot, s);
+      *nnz = int64_t(htot);
+      return fail(c, MCD_E_INVALID, "connections: capacity too small");
+    }
+    conn_kernel<false><<<grid_of(n, T), T, 0, s>>>(c->idx.B, *c->hp, nullptr, off, nullptr, rows, cols, vals, 1);
+    MCD_LAUNCHED(c);
+    conn_kernel<true><<<grid_of(n, T), T, 0, s>>>(c->idx.A, *c->hp, nullptr, off, cb, rows, cols, vals, 1);
+    MCD_LAUNCHED(c);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  cudaFreeAsync(ca, s); cudaFreeAsync(cb, s); cudaFreeAsync(off, s); cudaFreeAsync(tot, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "connections");
+  *nnz = int64_t(htot);
+  c->idx.nnz = int64_t(htot);
+  return MCD_OK;
+}
+
+}  // namespace mcd

@@ -1,0 +1,457 @@
+// extern "C" entry points declared in include/mcd.h: argument checks, state
+// handling and dispatch to the sampler, index, H*v and Lanczos code.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "mcd_internal.h"
+
+namespace mcd {
+
+int fail(mcd_ctx* c, int status, const std::string& msg) {
+  if (c) c->err = msg;
+  return status;
+}
+
+int cuda_fail(mcd_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, MCD_E_CUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+}  // namespace mcd
+
+using namespace mcd;
+
+namespace {
+
+const char* g_create_error = "";
+
+bool has_device(mcd_ctx* c) { return c->device >= 0; }
+
+int need_device(mcd_ctx* c) {
+  if (!has_device(c)) return fail(c, MCD_E_NODEVICE, "host-only context (device = -1)");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  return MCD_OK;
+}
+
+int need_basis(mcd_ctx* c) {
+  if (!c->has_ham) return fail(c, MCD_E_STATE, "no Hamiltonian set");
+  if (c->n_basis == 0) return fail(c, MCD_E_STATE, "no basis set");
+  return MCD_OK;
+}
+
+int install_basis(mcd_ctx* c, std::vector<uint64_t>&& words) {
+  c->basis = std::move(words);
+  c->n_basis = int64_t(c->basis.size());
+  c->basis_on_host = true;
+  if (has_device(c)) {
+    int st = need_device(c);
+    if (st != MCD_OK) return st;
+    st = build_index(c, c->basis.data(), c->n_basis, false);
+    if (st != MCD_OK) {
+      c->basis.clear();
+      c->n_basis = 0;
+      return st;
+    }
+  }
+  return MCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mcd_create(mcd_ctx** out, int device, void* cuda_stream) {
+  if (!out) return MCD_E_INVALID;
+  *out = nullptr;
+  mcd_ctx* c = new (std::nothrow) mcd_ctx();
+  if (!c) {
+    g_create_error = "out of host memory";
+    return MCD_E_OOM;
+  }
+  c->hp = new (std::nothrow) HamParams();
+  if (!c->hp) {
+    delete c;
+    g_create_error = "out of host memory";
+    return MCD_E_OOM;
+  }
+  std::memset(c->hp, 0, sizeof(HamParams));
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (device >= 0) {
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || device >= count) {
+      g_create_error = e != cudaSuccess ? cudaGetErrorString(e) : "device ordinal out of range";
+      delete c->hp;
+      delete c;
+      return e != cudaSuccess ? MCD_E_CUDA : MCD_E_INVALID;
+    }
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+      g_create_error = cudaGetErrorString(e);
+      delete c->hp;
+      delete c;
+      return MCD_E_CUDA;
+    }
+  } else if (device != -1) {
+    g_create_error = "device must be >= 0 or -1 (host only)";
+    delete c->hp;
+    delete c;
+    return MCD_E_INVALID;
+  }
+  *out = c;
+  return MCD_OK;
+}
+
+int mcd_destroy(mcd_ctx* c) {
+  if (!c) return MCD_OK;
+  if (has_device(c)) {
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_index(c->idx);
+    free_lanczos(c->lw);
+    if (c->d_eps) cudaFree(c->d_eps);
+    if (c->d_U) cudaFree(c->d_U);
+    if (c->tm) {
+      if (c->tm->created)
+        for (auto& ev : c->tm->ev) cudaEventDestroy(ev);
+      delete c->tm;
+    }
+  }
+  delete c->hp;
+  delete c;
+  return MCD_OK;
+}
+
+int mcd_set_stream(mcd_ctx* c, void* stream) {
+  if (!c) return MCD_E_INVALID;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return MCD_OK;
+}
+
+int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
+  if (!c) return MCD_E_INVALID;
+  switch (option) {
+    case MCD_OPT_HV_ALGO:
+      if (value != 0 && value != 1) return fail(c, MCD_E_INVALID, "HV_ALGO must be 0 or 1");
+      c->hv_algo = int(value);
+      return MCD_OK;
+    case MCD_OPT_KERNEL_TIMING:
+      if (value && has_device(c)) {
+        int st = need_device(c);
+        if (st != MCD_OK) return st;
+        if (!c->tm) c->tm = new (std::nothrow) Timing();
+        if (!c->tm) return fail(c, MCD_E_OOM, "timing");
+        if (!c->tm->created) {
+          for (auto& ev : c->tm->ev) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+          }
+          c->tm->created = true;
+        }
+      }
+      c->timing = value ? 1 : 0;
+      return MCD_OK;
+    case MCD_OPT_SAMPLER_THREADS:
+      if (value < 0 || value > 1024) return fail(c, MCD_E_INVALID, "SAMPLER_THREADS out of range");
+      c->sampler_threads = int(value);
+      return MCD_OK;
+    default:
+      return fail(c, MCD_E_INVALID, "unknown option");
+  }
+}
+
+const char* mcd_last_error(const mcd_ctx* c) { return c ? c->err.c_str() : g_create_error; }
+
+const char* mcd_status_string(int s) {
+  switch (s) {
+    case MCD_OK: return "ok";
+    case MCD_W_SHORT: return "sampler returned fewer states than asked";
+    case MCD_E_INVALID: return "invalid argument";
+    case MCD_E_SECTOR: return "state outside the sector";
+    case MCD_E_OOM: return "out of memory";
+    case MCD_E_CUDA: return "CUDA error";
+    case MCD_E_NOT_CONVERGED: return "not converged";
+    case MCD_E_BREAKDOWN: return "Lanczos breakdown";
+    case MCD_E_TIMEOUT: return "timeout";
+    case MCD_E_STATE: return "call out of order";
+    case MCD_E_NODEVICE: return "no device in this context";
+    default: return "unknown status";
+  }
+}
+
+int mcd_set_hamiltonian(mcd_ctx* c, int n, const double* t, const double* eps, const double* U, int U_len,
+                        int n_up, int n_dn) {
+  if (!c) return MCD_E_INVALID;
+  if (n < 1 || n > kMaxSites) return fail(c, MCD_E_INVALID, "n_sites must be in [1, 32]");
+  if (!t || !U) return fail(c, MCD_E_INVALID, "t and U are required");
+  if (U_len != 1 && U_len != n) return fail(c, MCD_E_INVALID, "U_len must be 1 or n_sites");
+  if (n_up < 0 || n_dn < 0 || n_up > n || n_dn > n) return fail(c, MCD_E_INVALID, "bad N_up / N_dn");
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double v = t[size_t(i) * n + j];
+      if (!std::isfinite(v)) return fail(c, MCD_E_INVALID, "non-finite t_ij");
+      if (i != j && v != t[size_t(j) * n + i]) return fail(c, MCD_E_INVALID, "t must be symmetric");
+    }
+  std::vector<double> e(n, 0.0), u(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    e[i] = eps ? eps[i] : 0.0;
+    u[i] = U[U_len == 1 ? 0 : i];
+    if (!std::isfinite(e[i]) || !std::isfinite(u[i])) return fail(c, MCD_E_INVALID, "non-finite eps or U");
+  }
+  const bool sector_changed = !c->has_ham || n != c->n || n_up != c->n_up || n_dn != c->n_dn;
+  c->n = n;
+  c->n_up = n_up;
+  c->n_dn = n_dn;
+  c->t.assign(t, t + size_t(n) * n);
+  c->eps = e;
+  c->U = u;
+  HamParams& hp = *c->hp;
+  std::memset(&hp, 0, sizeof(HamParams));
+  hp.n_sites = n;
+  int nb = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      const double v = t[size_t(i) * n + j];
+      if (v == 0.0) continue;
+      Bond& b = hp.bonds[nb++];
+      b.mask = (1u << i) | (1u << j);
+      b.between = (j - i > 1) ? (((j >= 32 ? 0u : (1u << j)) - 1u) & ~((1u << (i + 1)) - 1u)) : 0u;
+      b.t = v;
+      b.t_hi = float(v);
+      b.t_lo = float(v - double(b.t_hi));
+    }
+  hp.n_bonds = nb;
+  bool uniform = true;
+  for (int i = 1; i < n; ++i)
+    if (e[i] != e[0] || u[i] != u[0]) uniform = false;
+  hp.uniform = uniform ? 1 : 0;
+  if (uniform) {
+    for (int k = 0; k <= n; ++k) {
+      const double d = e[0] * double(n_up + n_dn) + u[0] * double(k);
+      hp.dtab[k] = d;
+      hp.dtab_hi[k] = float(d);
+      hp.dtab_lo[k] = float(d - double(hp.dtab_hi[k]));
+    }
+  }
+  if (has_device(c)) {
+    int st = need_device(c);
+    if (st != MCD_OK) return st;
+    if (!c->d_eps) {
+      cudaError_t er = cudaMalloc(&c->d_eps, sizeof(double) * kMaxSites);
+      if (er == cudaSuccess) er = cudaMalloc(&c->d_U, sizeof(double) * kMaxSites);
+      if (er != cudaSuccess) return cuda_fail(c, er, "cudaMalloc(eps, U)");
+    }
+    cudaError_t er = cudaMemcpy(c->d_eps, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (er == cudaSuccess) er = cudaMemcpy(c->d_U, u.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (er != cudaSuccess) return cuda_fail(c, er, "copy eps, U");
+    hp.eps = c->d_eps;
+    hp.U = c->d_U;
+  }
+  c->has_ham = true;
+  if (sector_changed) {
+    c->basis.clear();
+    c->n_basis = 0;
+    if (has_device(c)) free_index(c->idx);
+    free_lanczos(c->lw);
+  }
+  c->idx.nnz = -1;
+  return MCD_OK;
+}
+
+int mcd_build_basis(mcd_ctx* c, uint64_t seed, int64_t n_target, double beta, const uint64_t* seed_states,
+                    int64_t n_seed, int flags, int64_t* n_out) {
+  if (!c) return MCD_E_INVALID;
+  if (!c->has_ham) return fail(c, MCD_E_STATE, "no Hamiltonian set");
+  if (!seed_states || n_seed < 1) return fail(c, MCD_E_INVALID, "at least one seed state is required");
+  if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(c, MCD_E_INVALID, "beta must be finite and >= 0");
+  if (flags & ~MCD_SAMPLE_NEW_ONLY) return fail(c, MCD_E_INVALID, "unknown sampler flag");
+  if (n_target < 1 || double(n_target) > sector_size(c->n, c->n_up, c->n_dn))
+    return fail(c, MCD_E_INVALID, "n_target must be in [1, sector size]");
+  if (n_target > 0x7FFFFFFF) return fail(c, MCD_E_INVALID, "n_target above 2^31 - 1");
+  std::vector<uint64_t> F;
+  int st;
+  try {
+    st = sample_basis(c, seed, n_target, beta, seed_states, n_seed, flags, F);
+  } catch (const std::bad_alloc&) {
+    return fail(c, MCD_E_OOM, "sampler: out of host memory");
+  }
+  if (st < 0) return st;
+  int st2 = install_basis(c, std::move(F));
+  if (st2 != MCD_OK) return st2;
+  if (n_out) *n_out = c->n_basis;
+  if (st == MCD_W_SHORT) c->err = "sampler stopped early: no new states";
+  return st;
+}
+
+int mcd_set_basis(mcd_ctx* c, const uint64_t* w, int64_t n) {
+  if (!c) return MCD_E_INVALID;
+  if (!c->has_ham) return fail(c, MCD_E_STATE, "no Hamiltonian set");
+  if (!w || n < 1) return fail(c, MCD_E_INVALID, "basis must hold at least one word");
+  if (n > 0x7FFFFFFF) return fail(c, MCD_E_INVALID, "basis above 2^31 - 1 states");
+  const int ns = c->n;
+  const uint64_t half = ns == 32 ? 0xFFFFFFFFull : ((1ull << ns) - 1);
+  for (int64_t k = 0; k < n; ++k) {
+    if (k > 0 && w[k] <= w[k - 1]) return fail(c, MCD_E_INVALID, "basis words must be strictly ascending");
+    if (ns < 32 && (w[k] >> (2 * ns)) != 0) return fail(c, MCD_E_SECTOR, "word has bits above 2*n_sites");
+    if (__builtin_popcountll(w[k] >> ns) != c->n_up || __builtin_popcountll(w[k] & half) != c->n_dn)
+      return fail(c, MCD_E_SECTOR, "word outside the (N_up, N_dn) sector");
+  }
+  std::vector<uint64_t> v;
+  try {
+    v.assign(w, w + n);
+  } catch (const std::bad_alloc&) {
+    return fail(c, MCD_E_OOM, "out of host memory");
+  }
+  return install_basis(c, std::move(v));
+}
+
+int mcd_set_basis_device(mcd_ctx* c, const uint64_t* w, int64_t n) {
+  if (!c) return MCD_E_INVALID;
+  if (!c->has_ham) return fail(c, MCD_E_STATE, "no Hamiltonian set");
+  int st = need_device(c);
+  if (st != MCD_OK) return st;
+  if (!w || n < 1) return fail(c, MCD_E_INVALID, "basis must hold at least one word");
+  if (n > 0x7FFFFFFF) return fail(c, MCD_E_INVALID, "basis above 2^31 - 1 states");
+  if (reinterpret_cast<uintptr_t>(w) % 8) return fail(c, MCD_E_INVALID, "misaligned words");
+  c->basis.clear();
+  c->basis_on_host = false;
+  c->n_basis = 0;
+  st = build_index(c, w, n, true);
+  if (st != MCD_OK) return st;
+  c->n_basis = n;
+  return MCD_OK;
+}
+
+int mcd_get_basis(const mcd_ctx* cc, uint64_t* out, int64_t cap, int64_t* n) {
+  if (!cc || !n) return MCD_E_INVALID;
+  mcd_ctx* c = const_cast<mcd_ctx*>(cc);
+  *n = c->n_basis;
+  if (!out || cap <= 0 || c->n_basis == 0) return MCD_OK;
+  const int64_t k = std::min<int64_t>(cap, *n);
+  if (c->basis_on_host) {
+    std::memcpy(out, c->basis.data(), sizeof(uint64_t) * size_t(k));
+    return MCD_OK;
+  }
+  int st = need_device(c);
+  if (st != MCD_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(out, c->idx.words, sizeof(uint64_t) * size_t(k), cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? MCD_OK : cuda_fail(c, e, "copy basis to host");
+}
+
+int mcd_launch_count(const mcd_ctx* c, int64_t* n) {
+  if (!c || !n) return MCD_E_INVALID;
+  *n = c->launches;
+  return MCD_OK;
+}
+
+int mcd_basis_info(mcd_ctx* c, int64_t* n_states, int64_t* n_up_blocks, int64_t* n_dn_blocks,
+                   int64_t* nnz) {
+  if (!c) return MCD_E_INVALID;
+  int st = need_basis(c);
+  if (st != MCD_OK) return st;
+  if (n_states) *n_states = c->n_basis;
+  if (!has_device(c)) {
+    if (n_up_blocks || n_dn_blocks || nnz) return fail(c, MCD_E_NODEVICE, "index lives on the device");
+    return MCD_OK;
+  }
+  if (n_up_blocks) *n_up_blocks = c->idx.A.nblk;
+  if (n_dn_blocks) *n_dn_blocks = c->idx.B.nblk;
+  if (nnz) {
+    if (c->idx.nnz < 0) {
+      st = need_device(c);
+      if (st != MCD_OK) return st;
+      int64_t v = 0;
+      st = hv_connections(c, nullptr, nullptr, nullptr, 0, &v);
+      if (st != MCD_OK) return st;
+    }
+    *nnz = c->idx.nnz;
+  }
+  return MCD_OK;
+}
+
+int mcd_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype) {
+  if (!c) return MCD_E_INVALID;
+  int st = need_basis(c);
+  if (st != MCD_OK) return st;
+  if ((st = need_device(c)) != MCD_OK) return st;
+  if (!x || !y) return fail(c, MCD_E_INVALID, "null vector");
+  if (dtype != MCD_F64 && dtype != MCD_F32) return fail(c, MCD_E_INVALID, "dtype must be MCD_F64 or MCD_F32");
+  if (ncols < 1 || ld < ncols) return fail(c, MCD_E_INVALID, "need 1 <= ncols <= ld");
+  const size_t es = dtype == MCD_F64 ? 8 : 4;
+  const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ya = reinterpret_cast<uintptr_t>(y);
+  const uintptr_t bytes = uintptr_t(c->idx.n) * uintptr_t(ld) * es;
+  if (xa < ya + bytes && ya < xa + bytes) return fail(c, MCD_E_INVALID, "x and y overlap");
+  if (xa % es || ya % es) return fail(c, MCD_E_INVALID, "misaligned vector");
+  return hv_apply(c, x, y, ncols, ld, dtype, nullptr, 0);
+}
+
+int mcd_diagonal(mcd_ctx* c, double* diag) {
+  if (!c) return MCD_E_INVALID;
+  int st = need_basis(c);
+  if (st != MCD_OK) return st;
+  if ((st = need_device(c)) != MCD_OK) return st;
+  if (!diag) return fail(c, MCD_E_INVALID, "null output");
+  return hv_diagonal(c, diag);
+}
+
+int mcd_connections(mcd_ctx* c, int64_t* rows, int64_t* cols, double* vals, int64_t cap, int64_t* nnz) {
+  if (!c || !nnz) return MCD_E_INVALID;
+  int st = need_basis(c);
+  if (st != MCD_OK) return st;
+  if ((st = need_device(c)) != MCD_OK) return st;
+  if (rows && (!cols || !vals)) return fail(c, MCD_E_INVALID, "rows, cols and vals go together");
+  return hv_connections(c, rows, cols, vals, cap, nnz);
+}
+
+int mcd_lanczos_ground(mcd_ctx* c, int max_iter, double tol, uint64_t seed, int dtype, double* E0, void* psi,
+                       int* iters, double* residual) {
+  if (!c) return MCD_E_INVALID;
+  int st = need_basis(c);
+  if (st != MCD_OK) return st;
+  if ((st = need_device(c)) != MCD_OK) return st;
+  if (!E0 || !iters || !residual) return fail(c, MCD_E_INVALID, "null output pointer");
+  if (max_iter < 1 || max_iter > 100000) return fail(c, MCD_E_INVALID, "max_iter must be in [1, 100000]");
+  if (dtype != MCD_F64 && dtype != MCD_F32) return fail(c, MCD_E_INVALID, "dtype must be MCD_F64 or MCD_F32");
+  if (!std::isfinite(tol)) return fail(c, MCD_E_INVALID, "tol must be finite");
+  return lanczos_ground(c, max_iter, tol, seed, dtype, E0, psi, iters, residual);
+}
+
+int mcd_lanczos_coeffs(const mcd_ctx* c, double* a, double* b, int cap, int* m) {
+  if (!c || !m) return MCD_E_INVALID;
+  *m = int(c->last_a.size());
+  const int k = std::min(cap, *m);
+  for (int i = 0; i < k; ++i) {
+    if (a) a[i] = c->last_a[i];
+    if (b) b[i] = c->last_b[i];
+  }
+  return MCD_OK;
+}
+
+int mcd_kernel_times(mcd_ctx* c, double* ms, int64_t* count, int n_classes, int reset) {
+  if (!c) return MCD_E_INVALID;
+  if (n_classes < 0) return fail(c, MCD_E_INVALID, "n_classes < 0");
+  if (c->tm) {
+    timing_collect(c);
+    for (int i = 0; i < n_classes && i < kTimingClasses; ++i) {
+      if (ms) ms[i] = c->tm->ms[i];
+      if (count) count[i] = c->tm->count[i];
+    }
+    if (reset)
+      for (int i = 0; i < kTimingClasses; ++i) {
+        c->tm->ms[i] = 0;
+        c->tm->count[i] = 0;
+      }
+  } else {
+    for (int i = 0; i < n_classes && i < kTimingClasses; ++i) {
+      if (ms) ms[i] = 0;
+      if (count) count[i] = 0;
+    }
+  }
+  return MCD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Internal declarations of the MCD library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mcd.h"
+
+namespace mcd {
+
+constexpr int kMaxSites = 32;
+constexpr int kMaxBonds = kMaxSites * (kMaxSites - 1) / 2;   // 496
+constexpr int kItem = 1024;          // states per work item of the block kernels
+constexpr int kStageWords = 12288;   // minor words a CTA stages in shared memory
+constexpr int kTimingClasses = 4;
+
+// One undirected bond (i < j, t_ij != 0).  A state of one spin can hop along
+// it iff exactly one of its two sites is occupied; the hop flips both bits.
+struct Bond {
+  uint32_t mask;      // (1 << i) | (1 << j)
+  uint32_t between;   // sites strictly between i and j
+  double t;           // t_ij
+  float t_hi, t_lo;   // t_ij split into two floats (t_hi + t_lo == t to ~2^-48)
+};
+
+// Hamiltonian data passed to kernels by value (kernel parameter space).
+struct HamParams {
+  int n_sites;
+  int n_bonds;
+  int uniform;          // 1: diagonal = dtab[popc(up & dn)]
+  int pad;
+  double dtab[kMaxSites + 1];       // uniform diagonal by double occupancy
+  float dtab_hi[kMaxSites + 1];
+  float dtab_lo[kMaxSites + 1];
+  const double* eps;    // device [n] (non-uniform case)
+  const double* U;      // device [n] (non-uniform case)
+  Bond bonds[kMaxBonds];
+};
+
+// One of the two orderings of the basis used by the H*v kernels.
+//   up-major (A): basis order; blocks share an up word; minor = dn word.
+//   dn-major (B): stable order by dn word; blocks share a dn word; minor = up.
+struct Layout {
+  int64_t n = 0;
+  int64_t nblk = 0;
+  int64_t n_items = 0;
+  uint32_t* minor = nullptr;     // [n]
+  uint32_t* blk_off = nullptr;   // [nblk + 1]
+  uint32_t* blk_major = nullptr; // [nblk]
+  uint32_t* item_blk = nullptr;  // [n_items + 1] block of the first state of item i
+  uint32_t* perm = nullptr;      // [n] layout position -> basis index (B only)
+};
+
+struct DevIndex {
+  int64_t n = 0;
+  int64_t cap = 0;               // states the buffers below can hold
+  uint64_t* words = nullptr;     // [n] basis words (device)
+  Layout A, B;
+  int64_t nnz = -1;              // off-diagonal nonzeros (lazy)
+};
+
+struct LanczosWork {
+  int64_t n = 0;
+  int dtype = -1;
+  void* v[3] = {nullptr, nullptr, nullptr};   // rotating Krylov storage
+  double* scal = nullptr;        // device scalar area (see krylov.cu)
+  int scal_cap = 0;
+  double* partials = nullptr;    // per-CTA fp64 partial sums
+  unsigned int* ticket = nullptr;
+  int max_ctas = 0;
+};
+
+struct Timing {
+  cudaEvent_t ev[2 * 1024];
+  int n_ev = 0;
+  int cls[1024];
+  double ms[kTimingClasses] = {0, 0, 0, 0};
+  int64_t count[kTimingClasses] = {0, 0, 0, 0};
+  bool created = false;
+};
+
+}  // namespace mcd
+
+struct mcd_ctx {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // Hamiltonian
+  bool has_ham = false;
+  int n = 0, n_up = 0, n_dn = 0;
+  std::vector<double> t, eps, U;
+  mcd::HamParams* hp = nullptr;       // host copy (large struct)
+  double* d_eps = nullptr;
+  double* d_U = nullptr;
+  // Basis (host copy valid when basis_on_host; n_basis is authoritative)
+  std::vector<uint64_t> basis;
+  int64_t n_basis = 0;
+  bool basis_on_host = false;
+  int64_t launches = 0;
+  mcd::DevIndex idx;
+  // Krylov
+  mcd::LanczosWork lw;
+  std::vector<double> last_a, last_b;
+  // Options
+  int hv_algo = 0;
+  int timing = 0;
+  int sampler_threads = 0;
+  mcd::Timing* tm = nullptr;
+};
+
+namespace mcd {
+
+// error helpers (mcd_api.cu)
+int fail(mcd_ctx* c, int status, const std::string& msg);
+int cuda_fail(mcd_ctx* c, cudaError_t e, const char* where);
+
+// host sampler (sampler.cpp)
+int sample_basis(mcd_ctx* c, uint64_t seed, int64_t n_target, double beta,
+                 const uint64_t* seeds, int64_t n_seed, int flags,
+                 std::vector<uint64_t>& out);
+double sector_size(int n, int n_up, int n_dn);
+
+// host eigensolvers (tridiag.cpp)
+double tridiag_lowest(const double* a, const double* b, int m, double* vec /*nullable [m]*/);
+
+// device index (index.cu)
+int build_index(mcd_ctx* c, const uint64_t* words, int64_t n, bool on_device);
+void free_index(DevIndex& ix);
+
+// H*v (hv.cu)
+int hv_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype,
+             double* dot_partials, int dot_slot);
+int hv_diagonal(mcd_ctx* c, double* out);
+int hv_connections(mcd_ctx* c, int64_t* rows, int64_t* cols, double* vals, int64_t cap,
+                   int64_t* nnz);
+int hv_dot_ctas(mcd_ctx* c, int ncols, int dtype);
+
+// Lanczos (krylov.cu)
+int lanczos_ground(mcd_ctx* c, int max_iter, double tol, uint64_t seed, int dtype,
+                   double* E0, void* psi, int* iters, double* residual);
+void free_lanczos(LanczosWork& w);
+
+// timing helpers (hv.cu)
+void timing_begin(mcd_ctx* c, int cls);
+void timing_end(mcd_ctx* c);
+void timing_collect(mcd_ctx* c);
+
+}  // namespace mcd
+
+// count one kernel launch of context c
+#define MCD_LAUNCHED(c) (++(c)->launches)

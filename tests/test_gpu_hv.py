@@ -1,0 +1,214 @@
+"""GPU parity of the H~ x path through the C ABI against the oracle:
+connection lists and signs bit-exact, diagonal, y = H~ x within the rounding
+bound of the arithmetic, for fp64 and fp32 vectors, one and many columns,
+ragged widths, padded rows, both kernel variants and the edge cases (one
+state, an oversized block, 32 sites, site-dependent eps and U)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2509_22975_gb300 as pkg
+from oracle import fock, hamiltonian as H, sampler as S
+from workloads import configs as C, lattice as L, random_block
+
+from gpu_common import U32, U64, apply_bound, device_ctx, golden, model, row_terms_bound
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pkg.build()
+
+
+def n_bonds(t):
+    return int(np.count_nonzero(np.triu(t, 1)))
+
+
+def check_apply(ctx, P, t, ncols, dtype, ld=None, seed=0, offset=0):
+    n = P.n
+    ld = ncols if ld is None else ld
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    X = random_block(n, ncols, seed, dtype)
+    Xfull = np.zeros((n, ld), dtype=dtype)
+    Xfull[:, :ncols] = X
+    # optional element offset to make the rows unaligned
+    xbuf = torch.zeros(n * ld + offset, dtype=tdt, device=DEV)
+    ybuf = torch.full((n * ld + offset,), float("nan"), dtype=tdt, device=DEV)
+    xbuf[offset:] = torch.from_numpy(Xfull.reshape(-1)).to(DEV)
+    x = xbuf[offset:].view(n, ld)
+    y = ybuf[offset:].view(n, ld)
+    st = ctx.L.mcd_apply(ctx.h, x.data_ptr(), y.data_ptr(), ncols, ld,
+                         pkg.MCD_F64 if dtype == np.float64 else pkg.MCD_F32)
+    ctx._check(st)
+    torch.cuda.synchronize()
+    Y = y.cpu().numpy()[:, :ncols].astype(np.float64)
+    Xd = X.astype(np.float64)
+    ref = P.sparse() @ Xd
+    absHx = H.apply_abs(P, Xd)
+    u = U64 if dtype == np.float64 else U32
+    nt = row_terms_bound(n_bonds(t))
+    # computed side within nt*u, reference (scipy fp64) within nt*U64
+    bound = apply_bound(absHx, nt, u) + apply_bound(absHx, nt, U64)
+    err = np.abs(Y - ref)
+    assert np.all(err <= bound), (float(np.max(err)), float(np.max(err - bound)))
+    if ld > ncols:   # padding untouched
+        assert np.all(np.isnan(y.cpu().numpy()[:, ncols:]))
+    return float(np.max(err))
+
+
+@pytest.fixture(scope="module")
+def ring8():
+    w = C.ring8_u4()
+    ctx = device_ctx(w)
+    B = ctx.mcd_get_basis()
+    P = H.build(model(w), B)
+    return w, ctx, B, P
+
+
+@pytest.fixture(scope="module")
+def tilted12():
+    w = C.tilted12_u8()
+    ctx = device_ctx(w)
+    B = ctx.mcd_get_basis()
+    P = H.build(model(w), B)
+    return w, ctx, B, P
+
+
+def test_basis_matches_oracle_sampler(ring8, tilted12):
+    for w, ctx, B, P in (ring8, tilted12):
+        ref = S.sample_basis(w.n_sites, w.lat.t, w.U_sites, w.n_up, w.n_dn, w.n_f, w.beta,
+                             [w.seed_word()], seed=w.seed)
+        assert np.array_equal(B, ref)
+
+
+@pytest.mark.parametrize("which", ["ring8", "tilted12"])
+def test_connections_bit_exact(which, request):
+    w, ctx, B, P = request.getfixturevalue(which)
+    nnz = ctx.mcd_connections()
+    assert nnz == P.nnz_offdiag() == golden()[f"{which}_mc_nnz"]
+    rows = torch.empty(nnz, dtype=torch.int64, device=DEV)
+    cols = torch.empty(nnz, dtype=torch.int64, device=DEV)
+    vals = torch.empty(nnz, dtype=torch.float64, device=DEV)
+    assert ctx.mcd_connections(rows, cols, vals) == nnz
+    r, c, v = rows.cpu().numpy(), cols.cpu().numpy(), vals.cpu().numpy()
+    o = np.lexsort((c, r))
+    assert np.array_equal(r[o], P.rows) and np.array_equal(c[o], P.cols)
+    assert np.array_equal(v[o], P.vals)          # t_ij * sign: exact
+    info = ctx.mcd_basis_info()
+    assert info["nnz_offdiag"] == nnz and info["n_states"] == len(B)
+    up, dn = fock.split(B, w.n_sites)
+    assert info["n_up_blocks"] == len(np.unique(up)) and info["n_dn_blocks"] == len(np.unique(dn))
+
+
+@pytest.mark.parametrize("which", ["ring8", "tilted12"])
+def test_diagonal(which, request):
+    w, ctx, B, P = request.getfixturevalue(which)
+    d = torch.empty(len(B), dtype=torch.float64, device=DEV)
+    ctx.mcd_diagonal(d)
+    assert np.array_equal(d.cpu().numpy(), P.diag)   # integer-valued here: exact
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("ncols", [1, 3, 8, 24, 48])
+def test_apply_ring8(ring8, dtype, ncols):
+    w, ctx, B, P = ring8
+    check_apply(ctx, P, w.lat.t, ncols, dtype, seed=ncols)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("ncols,ld,offset", [(1, 1, 0), (12, 12, 0), (24, 24, 0), (5, 8, 0),
+                                             (4, 4, 1), (130, 132, 0)])
+def test_apply_tilted12(tilted12, dtype, ncols, ld, offset):
+    w, ctx, B, P = tilted12
+    check_apply(ctx, P, w.lat.t, ncols, dtype, ld=ld, offset=offset, seed=7 + ncols)
+
+
+def test_apply_exact_rows_fsum(ring8):
+    # against correctly rounded rows (math.fsum) on the small case
+    w, ctx, B, P = ring8
+    X = random_block(len(B), 2, 3, np.float64)
+    x = torch.from_numpy(X).to(DEV)
+    y = torch.empty_like(x)
+    ctx.mcd_apply(x, y)
+    torch.cuda.synchronize()
+    ref = H.apply_exact(P, X)
+    bound = apply_bound(H.apply_abs(P, X), row_terms_bound(n_bonds(w.lat.t)), U64)
+    assert np.all(np.abs(y.cpu().numpy() - ref) <= bound)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_plain_kernel_variant(tilted12, dtype):
+    w, ctx, B, P = tilted12
+    ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, 1)
+    try:
+        check_apply(ctx, P, w.lat.t, 2, dtype, seed=99)
+    finally:
+        ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, 0)
+
+
+def test_single_state_basis():
+    w = C.ring8_u4()
+    ctx = device_ctx(w, basis=np.array([w.seed_word()], dtype=np.uint64))
+    P = H.build(model(w), np.array([w.seed_word()], dtype=np.uint64))
+    check_apply(ctx, P, w.lat.t, 3, np.float64)
+
+
+def test_oversized_block_uses_global_search():
+    # one up word with all C(16, 8) = 12870 down words: a block larger than
+    # the shared-memory staging area of a CTA
+    lat = L.ring(16)
+    w = C.Workload("ring16", lat, 8.0, 8, 8, 0, 0.2)
+    ups = fock.words_with_popcount(16, 8)
+    dns = np.array(fock.words_with_popcount(16, 8), dtype=np.uint64)
+    big = (np.uint64(ups[100]) << np.uint64(16)) | dns
+    rng = np.random.default_rng(4)
+    others = [(np.uint64(ups[k]) << np.uint64(16)) | dns[rng.choice(len(dns), 300, replace=False)]
+              for k in (3, 99, 101, 2000)]
+    B = np.unique(np.concatenate([big] + others))
+    ctx = device_ctx(w, basis=B)
+    P = H.build(model(w), B)
+    for dt in (np.float64, np.float32):
+        check_apply(ctx, P, lat.t, 1, dt)
+        check_apply(ctx, P, lat.t, 6, dt)
+
+
+def test_thirty_two_sites_random_hoppings_and_site_terms():
+    # 32 sites (words use all 64 bits), random long-range t_ij, site-dependent
+    # eps_i and U_i (non-uniform diagonal path)
+    n = 32
+    rng = np.random.default_rng(8)
+    t = np.zeros((n, n))
+    for _ in range(60):
+        i, j = rng.choice(n, 2, replace=False)
+        t[i, j] = t[j, i] = rng.normal()
+    lat = L.Lattice("rand32", n, t, np.zeros((n, 2), int), np.arange(n) % 2)
+    eps = rng.normal(size=n)
+    U = rng.uniform(0, 8, size=n)
+    w = C.Workload("rand32", lat, 0.0, 3, 2, 0, 0.5)
+    seed = (np.uint64(0b111 << 29) << np.uint64(32)) | np.uint64(0b11)
+    B = S.sample_basis(n, t, U, 3, 2, 20000, 0.5, [int(seed)], seed=1)
+    import paper_2509_22975_gb300 as pk
+    ctx = pk.Context(0)
+    ctx.mcd_set_hamiltonian(t, eps, U, 3, 2)
+    ctx.mcd_set_basis(B)
+    P = H.build(H.Model(n, t, eps, U), B)
+    d = torch.empty(len(B), dtype=torch.float64, device=DEV)
+    ctx.mcd_diagonal(d)
+    assert np.max(np.abs(d.cpu().numpy() - P.diag)) <= 4 * n * U64 * np.max(np.abs(P.diag))
+    nnz = ctx.mcd_connections()
+    assert nnz == P.nnz_offdiag()
+    for dt in (np.float64, np.float32):
+        check_apply(ctx, P, t, 1, dt, seed=2)
+        check_apply(ctx, P, t, 8, dt, seed=3)
+
+
+def test_argument_errors(ring8):
+    w, ctx, B, P = ring8
+    x = torch.zeros(len(B), dtype=torch.float64, device=DEV)
+    for args, code in [((x.data_ptr(), x.data_ptr(), 1, 1, 0), -1),           # aliasing
+                       ((x.data_ptr(), x.data_ptr() + 8 * len(B), 0, 1, 0), -1),   # ncols 0
+                       ((x.data_ptr(), x.data_ptr() + 8 * len(B), 2, 1, 0), -1),   # ld < ncols
+                       ((x.data_ptr(), x.data_ptr() + 8 * len(B), 1, 1, 7), -1)]:  # dtype
+        assert ctx.L.mcd_apply(ctx.h, *args) == code

@@ -1,0 +1,130 @@
+"""GPU Lanczos (App. B) through the C ABI: E0 against the oracle's dense and
+Lanczos ground states (1e-10 relative in fp64, 1e-6 absolute in fp32), the
+full-sector pins, the Ritz vector and its residual, determinism, the
+single-state breakdown and the full-size 4x4 run (fp32 vs fp64)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2509_22975_gb300 as pkg
+from oracle import fock, hamiltonian as H, lanczos as LZ
+from workloads import configs as C
+
+from gpu_common import device_ctx, golden, model
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pkg.build()
+
+
+@pytest.mark.parametrize("dtype,tol", [(pkg.MCD_F64, 1e-10), (pkg.MCD_F32, 1e-6)])
+def test_ring8_mc_basis(dtype, tol):
+    w = C.ring8_u4()
+    ctx = device_ctx(w)
+    B = ctx.mcd_get_basis()
+    P = H.build(model(w), B)
+    E_ref, v_ref, _ = LZ.dense_ground(P.dense())
+    assert abs(E_ref - golden()["ring8_mc_E0"]) < 1e-12
+    tdt = torch.float64 if dtype == pkg.MCD_F64 else torch.float32
+    psi = torch.empty(len(B), dtype=tdt, device=DEV)
+    r = ctx.mcd_lanczos_ground(400, 1e-12 if dtype == pkg.MCD_F64 else 1e-7, 0, dtype, psi=psi,
+                               allow_not_converged=dtype == pkg.MCD_F32)
+    if dtype == pkg.MCD_F64:
+        assert abs(r["E0"] - E_ref) <= tol * abs(E_ref)
+        assert r["residual"] < 1e-8
+    else:
+        assert abs(r["E0"] - E_ref) <= tol
+        assert r["residual"] < 1e-3
+    ov = abs(float(psi.double().cpu().numpy() @ v_ref))
+    assert ov > 1 - (1e-10 if dtype == pkg.MCD_F64 else 1e-5)
+    a, b = ctx.mcd_lanczos_coeffs()
+    assert len(a) == r["iters"] and b[0] == 0.0 and np.all(b[1:] > 0)
+
+
+def test_ring8_full_sector_pin():
+    w = C.ring8_u4()
+    ctx = device_ctx(w, basis=fock.sector(8, 4, 4))
+    r = ctx.mcd_lanczos_ground(500, 1e-12, 1, pkg.MCD_F64)
+    assert abs(r["E0"] - golden()["ring8_full_E0"]) < 1e-10 * 4.6
+    assert abs(r["E0"] - (-4.603526299989)) < 1e-11
+
+
+def test_tilted12_full_sector_pins():
+    # full 853,776-state sector: the oracle's value, and the paper's printed
+    # per-site energy at mu = U/2 (Table of 2D energies, 12 sites, -4.5226)
+    w = C.tilted12_u8()
+    ctx = device_ctx(w, basis=fock.sector(12, 6, 6))
+    r = ctx.mcd_lanczos_ground(800, 1e-12, 2, pkg.MCD_F64)
+    E = r["E0"]
+    assert abs(E - golden()["tilted12_full_E0"]) <= 1e-10 * abs(E)
+    assert math.trunc((E - 4.0 * 12) / 12 * 1e4) / 1e4 == -4.5226
+
+
+@pytest.mark.parametrize("dtype", [pkg.MCD_F64, pkg.MCD_F32])
+def test_tilted12_mc_basis(dtype):
+    w = C.tilted12_u8()
+    ctx = device_ctx(w)
+    r = ctx.mcd_lanczos_ground(800, 1e-12 if dtype == pkg.MCD_F64 else 1e-8, 0, dtype,
+                               allow_not_converged=dtype == pkg.MCD_F32)
+    E_ref = golden()["tilted12_mc_E0"]
+    if dtype == pkg.MCD_F64:
+        assert abs(r["E0"] - E_ref) <= 1e-10 * abs(E_ref)
+    else:
+        assert abs(r["E0"] - E_ref) <= 1e-6
+
+
+def test_deterministic_and_plain_variant_agree():
+    w = C.tilted12_u8()
+    ctx = device_ctx(w, nf=50000)
+    r1 = ctx.mcd_lanczos_ground(60, 0.0, 5, pkg.MCD_F64)
+    a1, b1 = ctx.mcd_lanczos_coeffs()
+    r2 = ctx.mcd_lanczos_ground(60, 0.0, 5, pkg.MCD_F64)
+    a2, b2 = ctx.mcd_lanczos_coeffs()
+    assert r1["iters"] == r2["iters"] == 60
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2)      # bit-identical reruns
+    ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, 1)
+    r3 = ctx.mcd_lanczos_ground(400, 1e-12, 5, pkg.MCD_F64)
+    ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, 0)
+    r4 = ctx.mcd_lanczos_ground(400, 1e-12, 5, pkg.MCD_F64)
+    assert abs(r3["E0"] - r4["E0"]) < 1e-10 * abs(r4["E0"])
+
+
+def test_single_state_breakdown():
+    w = C.ring8_u4()
+    word = np.array([w.seed_word()], dtype=np.uint64)
+    ctx = device_ctx(w, basis=word)
+    d = H.build(model(w), word).diag[0]
+    psi = torch.empty(1, dtype=torch.float64, device=DEV)
+    r = ctx.mcd_lanczos_ground(50, 1e-12, 0, pkg.MCD_F64, psi=psi)
+    assert r["iters"] == 1 and r["E0"] == d and abs(abs(float(psi.item())) - 1) < 1e-15
+
+
+def test_argument_errors():
+    w = C.ring8_u4()
+    ctx = device_ctx(w, nf=300)
+    with pytest.raises(pkg.MCDError):
+        ctx.mcd_lanczos_ground(0, 1e-10, 0, pkg.MCD_F64)
+    with pytest.raises(pkg.MCDError):
+        ctx.mcd_lanczos_ground(10, 1e-10, 0, 5)
+    r = ctx.mcd_lanczos_ground(3, 1e-14, 0, pkg.MCD_F64, allow_not_converged=True)
+    assert r["status"] == pkg.MCDError(0, "").status or r["status"] in (0, -5)
+
+
+@pytest.mark.slow
+def test_square16_full_size_fp32_vs_fp64():
+    # the 4x4 t-t' workload at its full 1e7-state basis: 200 Lanczos steps in
+    # fp32 vectors and in fp64; |E0_fp32 - E0_fp64| < 1e-6, E0 above the
+    # smaller nested basis' value is impossible (variational, nested bases)
+    w = C.square16_u8()
+    ctx = device_ctx(w)
+    assert ctx.mcd_basis_info(nnz=False)["n_states"] == w.n_f
+    r64 = ctx.mcd_lanczos_ground(200, 0.0, 0, pkg.MCD_F64)
+    r32 = ctx.mcd_lanczos_ground(200, 0.0, 0, pkg.MCD_F32)
+    assert abs(r32["E0"] - r64["E0"]) < 1e-6, (r32, r64)
+    assert r64["E0"] < golden()["square16_mc65536_E0"]
