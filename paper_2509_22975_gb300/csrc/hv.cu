@@ -571,7 +571,10 @@ int hv_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, d
     MCD_LAUNCHED(c);
     timing_end(c);
     e = cudaGetLastError();
-    return e == cudaSuccess ? MCD_OK : cuda_fail(c, e, "plain H*v launch");
+    if (e != cudaSuccess) return cuda_fail(c, e, "plain H*v launch");
+    // the block kernels fuse <x, H x> into their last pass; here it is separate
+    if (dot_partials) return vec_dot(c, x, y, c->idx.n, dtype, c->lw.scal + dot_slot);
+    return MCD_OK;
   }
   unsigned int* ticket = nullptr;
   double* dot_out = nullptr;

@@ -384,6 +384,20 @@ void free_lanczos(LanczosWork& w) {
   w = LanczosWork();
 }
 
+int vec_dot(mcd_ctx* c, const void* a, const void* b, int64_t n, int dtype, double* out) {
+  LanczosWork& w = c->lw;
+  const int vg = vec_grid(n);
+  if (dtype == MCD_F64)
+    dot_kernel<double><<<vg, kThreads, 0, c->stream>>>(static_cast<const double*>(a), static_cast<const double*>(b),
+                                                       n, w.partials, w.ticket, out);
+  else
+    dot_kernel<float><<<vg, kThreads, 0, c->stream>>>(static_cast<const float*>(a), static_cast<const float*>(b), n,
+                                                      w.partials, w.ticket, out);
+  MCD_LAUNCHED(c);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MCD_OK : cuda_fail(c, e, "dot");
+}
+
 int lanczos_ground(mcd_ctx* c, int max_iter, double tol, uint64_t seed, int dtype, double* E0, void* psi,
                    int* iters, double* residual) {
   int st = ensure_work(c, dtype, max_iter);

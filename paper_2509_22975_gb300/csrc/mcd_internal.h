@@ -142,6 +142,8 @@ int hv_dot_ctas(mcd_ctx* c, int ncols, int dtype);
 int lanczos_ground(mcd_ctx* c, int max_iter, double tol, uint64_t seed, int dtype,
                    double* E0, void* psi, int* iters, double* residual);
 void free_lanczos(LanczosWork& w);
+// *out (device) = sum_k a[k] b[k] over n elements of dtype, fixed-order reduction
+int vec_dot(mcd_ctx* c, const void* a, const void* b, int64_t n, int dtype, double* out);
 
 // timing helpers (hv.cu)
 void timing_begin(mcd_ctx* c, int cls);
