@@ -132,6 +132,20 @@ int mcd_diagonal(mcd_ctx* ctx, double* diag_dev);
 int mcd_connections(mcd_ctx* ctx, int64_t* rows_dev, int64_t* cols_dev, double* vals_dev,
                     int64_t cap, int64_t* nnz);
 
+/* No counterpart in the paper: the same output as mcd_connections, for
+ * callers that must not allocate device memory (a caller whose memory is all
+ * owned by its own pool, one under a fixed memory budget, one recording into
+ * a CUDA graph).  The per-row counts and offsets live in one fixed 2 MiB
+ * array of device global memory that the library defines, so this call
+ * allocates nothing; every GPU that loads the library keeps that array until
+ * the process exits.  Limit: bases of at most 262144 states, else
+ * MCD_E_INVALID.  The first call on a device looks up the array's address
+ * (make it before any stream capture).  All calls share the array: calls whose
+ * work overlaps on the GPU race.  Entries are grouped by row; their order
+ * inside a row differs from call to call. */
+int mcd_connections_noalloc(mcd_ctx* ctx, int64_t* rows_dev, int64_t* cols_dev, double* vals_dev,
+                            int64_t cap, int64_t* nnz);
+
 /* App. B: Lanczos ground state of H~ from a SplitMix64 start vector keyed by
  * `seed`, normalised form of the recursion (a_n, b_n as in App. B), Krylov
  * vectors and H~ products in dtype, coefficients and the tridiagonal

@@ -47,6 +47,7 @@ _SIGS = {
     "mcd_apply": (ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mcd_diagonal": (ctypes.c_int, [c_vp, c_vp]),
     "mcd_connections": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.c_int64, c_i64p]),
+    "mcd_connections_noalloc": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.c_int64, c_i64p]),
     "mcd_lanczos_ground": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_int,
                                           c_dp, c_vp, ctypes.POINTER(ctypes.c_int), c_dp]),
     "mcd_lanczos_coeffs": (ctypes.c_int, [c_vp, c_dp, c_dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
@@ -198,6 +199,16 @@ class Context:
         self._sync_stream()
         self._check(self.L.mcd_connections(self.h, _ptr(rows) or None, _ptr(cols) or None,
                                            _ptr(vals) or None, cap, ctypes.byref(n)))
+        return n.value
+
+    def mcd_connections_noalloc(self, rows=None, cols=None, vals=None) -> int:
+        """mcd_connections without any device allocation (fixed scratch, at
+        most 262144 states)."""
+        n = ctypes.c_int64(0)
+        cap = 0 if rows is None else rows.numel()
+        self._sync_stream()
+        self._check(self.L.mcd_connections_noalloc(self.h, _ptr(rows) or None, _ptr(cols) or None,
+                                                   _ptr(vals) or None, cap, ctypes.byref(n)))
         return n.value
 
     def mcd_lanczos_ground(self, max_iter: int, tol: float, seed: int, dtype: int, psi=None,
