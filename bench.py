@@ -294,11 +294,11 @@ def main():
         ctx.mcd_set_basis(words)
         re2e = ctx.mcd_lanczos_ground(args.iters, 0.0, 0, pkg.MCD_F32)
         _E0 = re2e["E0"]
-    e2e_s = (time.perf_counter() - h0) / args.e2e_steps
+    e2e_s = (time.perf_counter() - h0) / max(args.e2e_steps, 1)
     chunks = list(range(16, args.iters + 1, 16)) + ([args.iters] if args.iters % 16 else [])
     d2h = sum(8 * (2 * m + 1) for m in chunks) + 8 + 4 + 16   # a/b read-backs, E0, checks, block counts
     h2d = n * 8
-    e2e = {"value": world * conns_per_step / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e = {"value": world * conns_per_step / e2e_s / 1e9 if args.e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
            "path": "mcd_set_basis(host words) + mcd_lanczos_ground + E0 to host"}
 

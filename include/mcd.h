@@ -59,8 +59,11 @@ typedef enum { MCD_F64 = 0, MCD_F32 = 1 } mcd_dtype;
 #define MCD_SAMPLE_NEW_ONLY 1   /* next starting points = new states only */
 
 /* Options (mcd_set_option). */
-#define MCD_OPT_HV_ALGO 1       /* 0 = two-layout block kernels (default),
-                                   1 = plain per-state global binary search   */
+#define MCD_OPT_HV_ALGO 1       /* 0 = two-layout block kernels, in-block
+                                   lookup by shared bitmap when n_sites <= 16,
+                                   by binary search otherwise (default);
+                                   1 = plain per-state global binary search;
+                                   2 = two-layout block kernels, binary search */
 #define MCD_OPT_KERNEL_TIMING 2 /* 1 = record CUDA events around H*v launches */
 #define MCD_OPT_SAMPLER_THREADS 3 /* host threads of the sampler (0 = auto)  */
 

@@ -25,6 +25,8 @@ namespace mcd {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kBitmapMaxSites = 16;            // 2^16-bit bitmap = 8 KiB of shared memory
+constexpr int kStageXBytes = 52 * 1024;        // x staging area of the bitmap kernel
 
 struct HvArgs {
   const void* x;
@@ -36,6 +38,12 @@ struct HvArgs {
   double* dot_partials;   // pass A, single column: per-CTA sum x[k] y[k]
   unsigned int* ticket;
   double* dot_out;
+  // bitmap kernel: dynamic shared-memory carve-up (bytes) and sizes
+  int nbp;                // bonds rounded up to a multiple of 4
+  int nw;                 // bitmap words = max(1, 2^n_sites / 32)
+  int off_bm, off_pre, off_xs;
+  int xs_cap;             // elements of T that fit in the x staging area
+  int ncp;                // staged row stride: ncols rounded up to VEC
 };
 
 template <typename T, int VEC>
@@ -357,6 +365,202 @@ __global__ void __launch_bounds__(kThreads) hv_block_kernel(const HvArgs a, cons
 }
 
 // ---------------------------------------------------------------------------------
+// Bitmap variant for n_sites <= 16.  For each block (states sharing the major
+// word) the CTA marks the minor words of all its states in a 2^n-bit shared
+// bitmap and stores, per 32-bit bitmap word, the block-local index of the
+// first state in it.  A hop target m2 is then in the basis iff its bit is set,
+// and its block-local index is pre[m2 >> 5] + popc(bits of that word below
+// m2): one shared load decides membership, a second gives the position.  The
+// x rows of the block are staged in shared memory when they fit, so the
+// gathers of found targets are shared loads too.  The CTA clears the bits it
+// set before moving to the next block.
+template <typename T, int VEC, int G, bool PASS_A, bool DOT>
+__global__ void __launch_bounds__(kThreads) hv_bitmap_kernel(const HvArgs a, const HamParams hp) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __shared__ uint32_t s_b0, s_b1;
+  __shared__ double s_red[kThreads / 32];
+  const int nbp = a.nbp;
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(s_dyn);
+  uint32_t* s_betw = s_mask + nbp;
+  float* s_thi = reinterpret_cast<float*>(s_betw + nbp);
+  float* s_tlo = s_thi + nbp;
+  double* s_t64 = reinterpret_cast<double*>(s_tlo + nbp);
+  uint32_t* bm = reinterpret_cast<uint32_t*>(s_dyn + a.off_bm);
+  uint16_t* pre = reinterpret_cast<uint16_t*>(s_dyn + a.off_pre);
+  T* xs = reinterpret_cast<T*>(s_dyn + a.off_xs);
+
+  const Layout& L = a.L;
+  const int item = blockIdx.x;
+  const int64_t k0 = int64_t(item) * kItem;
+  const int64_t k1 = (k0 + kItem < L.n) ? k0 + kItem : L.n;
+  const int nbonds = hp.n_bonds;
+  for (int b = threadIdx.x; b < nbonds; b += kThreads) {
+    s_mask[b] = hp.bonds[b].mask;
+    s_betw[b] = hp.bonds[b].between;
+    s_thi[b] = hp.bonds[b].t_hi;
+    s_tlo[b] = hp.bonds[b].t_lo;
+    s_t64[b] = hp.bonds[b].t;
+  }
+  for (int i = threadIdx.x; i < a.nw; i += kThreads) bm[i] = 0u;
+  if (threadIdx.x == 0) {
+    const uint32_t b0 = L.item_blk[item];
+    uint32_t b1 = L.item_blk[item + 1];
+    if (b1 == uint32_t(L.nblk) || L.blk_off[b1] == uint32_t(k1)) b1 -= 1;
+    s_b0 = b0;
+    s_b1 = b1;
+  }
+  __syncthreads();
+  const uint32_t b0 = s_b0, b1 = s_b1;
+
+  const T* __restrict__ x = static_cast<const T*>(a.x);
+  T* __restrict__ y = static_cast<T*>(a.y);
+  const int lane = threadIdx.x & 31;
+  const int g = lane % G;
+  const int group = threadIdx.x / G;
+  constexpr int kGroups = kThreads / G;
+  const int ncols = a.ncols, ld = a.ld, ncp = a.ncp;
+  const int ctile = G * VEC;
+  double dot_acc = 0.0;
+
+  for (uint32_t blk = b0; blk <= b1; ++blk) {
+    const int bs = int(L.blk_off[blk]), be = int(L.blk_off[blk + 1]);
+    const uint32_t major = L.blk_major[blk];
+    const int bsz = be - bs;
+    const bool staged = int64_t(bsz) * ncp <= a.xs_cap;
+    for (int q = threadIdx.x; q < bsz; q += kThreads) {
+      const uint32_t d = L.minor[bs + q];
+      atomicOr(&bm[d >> 5], 1u << (d & 31));
+      if (q == 0 || (L.minor[bs + q - 1] >> 5) != (d >> 5)) pre[d >> 5] = uint16_t(q);
+    }
+    if (staged) {
+      if (ncp == 1) {
+        for (int q = threadIdx.x; q < bsz; q += kThreads)
+          xs[q] = x[int64_t(PASS_A ? bs + q : int(L.perm[bs + q])) * ld];
+      } else {
+        for (int e = threadIdx.x; e < bsz * ncp; e += kThreads) {
+          const int q = e / ncp, cc = e - q * ncp;
+          const int64_t row = PASS_A ? int64_t(bs + q) : int64_t(L.perm[bs + q]);
+          xs[e] = cc < ncols ? x[row * ld + cc] : T(0);
+        }
+      }
+    }
+    __syncthreads();
+    const int lo = (int64_t(bs) > k0) ? bs : int(k0);
+    const int hi = (int64_t(be) < k1) ? be : int(k1);
+    const int rounds = (hi - lo + kGroups - 1) / kGroups;
+    using C = ChunkOf<T, VEC>;
+    for (int r = 0; r < rounds; ++r) {
+      const int k = lo + r * kGroups + group;
+      const bool live = k < hi;
+      const uint32_t m = live ? L.minor[k] : 0u;
+      for (int c0 = 0; c0 < ncols; c0 += ctile) {
+        const int col = c0 + g * VEC;
+        const int cvalid = ncols - col;
+        Acc<T> acc[VEC];
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) acc[c].zero();
+        for (int bb = 0; bb < nbonds; bb += G) {
+          const int b = bb + g;
+          int q = -1;
+          Coef<T> cf{T(0), T(0)};
+          if (live && b < nbonds) {
+            const uint32_t mk = s_mask[b];
+            if (__popc(m & mk) == 1) {
+              const uint32_t m2 = m ^ mk;
+              const uint32_t wd = bm[m2 >> 5];
+              const uint32_t bit = m2 & 31u;
+              if ((wd >> bit) & 1u) {
+                q = int(pre[m2 >> 5]) + __popc(wd & ((1u << bit) - 1u));
+                cf = bond_coef<T>(s_thi, s_tlo, s_t64, b, __popc(m & s_betw[b]) & 1);
+              }
+            }
+          }
+#pragma unroll
+          for (int s = 0; s < G; ++s) {
+            const int qq = G == 1 ? q : __shfl_sync(0xffffffffu, q, s, G);
+            const T ch = G == 1 ? cf.hi : __shfl_sync(0xffffffffu, cf.hi, s, G);
+            const T cl = G == 1 ? cf.lo : __shfl_sync(0xffffffffu, cf.lo, s, G);
+            if (qq >= 0 && cvalid > 0) {
+              T xv[VEC];
+              if (staged) {
+                const T* p = xs + qq * ncp + col;
+                if (VEC == 1 || cvalid >= VEC) {
+#pragma unroll
+                  for (int c = 0; c < VEC; ++c) xv[c] = p[c];
+                } else {
+#pragma unroll
+                  for (int c = 0; c < VEC; ++c) xv[c] = c < cvalid ? p[c] : T(0);
+                }
+              } else {
+                const int64_t row = PASS_A ? int64_t(bs + qq) : int64_t(L.perm[bs + qq]);
+                C::load(x + row * ld + col, cvalid, xv);
+              }
+#pragma unroll
+              for (int c = 0; c < VEC; ++c) acc[c].fma(ch, cl, xv[c]);
+            }
+          }
+        }
+        if (live && cvalid > 0) {
+          T out[VEC];
+          if (PASS_A) {
+            const Coef<T> dc = diag_coef<T>(hp, major, m);
+            T xv[VEC], yv[VEC];
+            C::load(x + int64_t(k) * ld + col, cvalid, xv);
+            C::load(y + int64_t(k) * ld + col, cvalid, yv);
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) {
+              acc[c].fma(dc.hi, dc.lo, xv[c]);
+              out[c] = acc[c].value() + yv[c];
+            }
+            if (DOT) dot_acc += double(xv[0]) * double(out[0]);
+            C::store(y + int64_t(k) * ld + col, cvalid, out);
+          } else {
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) out[c] = acc[c].value();
+            C::store(y + int64_t(L.perm[k]) * ld + col, cvalid, out);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < bsz; q += kThreads) bm[L.minor[bs + q] >> 5] = 0u;
+    __syncthreads();
+  }
+
+  if (DOT) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot_acc += __shfl_xor_sync(0xffffffffu, dot_acc, o);
+    if (lane == 0) s_red[threadIdx.x >> 5] = dot_acc;
+    __syncthreads();
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
+      a.dot_partials[blockIdx.x] = sum;
+      __threadfence();
+      const unsigned t = atomicAdd(a.ticket, 1u);
+      s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+      double sum = 0.0;
+      for (int i = threadIdx.x; i < int(gridDim.x); i += kThreads) sum += __ldcg(a.dot_partials + i);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      __syncthreads();
+      if (lane == 0) s_red[threadIdx.x >> 5] = sum;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) tot += s_red[w];
+        *a.dot_out = tot;
+        *a.ticket = 0u;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // Plain path: one thread per state, both spins, binary search over the whole
 // sorted basis in global memory.  Kept as the simple reference GPU path.
 template <typename T>
@@ -483,27 +687,54 @@ cudaError_t launch_pair(mcd_ctx* c, const void* x, void* y, int ncols, int ld, d
   a.dot_partials = partials;
   a.ticket = ticket;
   a.dot_out = dot_out;
-  const size_t smem = kStageWords * sizeof(uint32_t);
-  static bool configured = false;   // per instantiation
-  if (!configured) {
-    cudaFuncSetAttribute(hv_block_kernel<T, VEC, G, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    cudaFuncSetAttribute(hv_block_kernel<T, VEC, G, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    cudaFuncSetAttribute(hv_block_kernel<T, VEC, G, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    configured = true;
+  const bool bitmap = c->n <= kBitmapMaxSites && c->hv_algo == 0;
+  size_t smem = kStageWords * sizeof(uint32_t);
+  if (bitmap) {
+    a.nbp = (c->hp->n_bonds + 3) & ~3;
+    a.nw = c->n >= 5 ? (1 << (c->n - 5)) : 1;
+    a.off_bm = 24 * a.nbp;
+    a.off_pre = a.off_bm + 4 * a.nw;
+    a.off_xs = (a.off_pre + 2 * a.nw + 15) & ~15;
+    a.ncp = ((ncols + VEC - 1) / VEC) * VEC;
+    a.xs_cap = int(kStageXBytes / sizeof(T));
+    smem = size_t(a.off_xs) + kStageXBytes;
+  }
+  static int configured_smem = -1;   // per instantiation; one device per process in practice
+  if (configured_smem < int(smem)) {
+    if (bitmap) {
+      cudaFuncSetAttribute(hv_bitmap_kernel<T, VEC, G, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      cudaFuncSetAttribute(hv_bitmap_kernel<T, VEC, G, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      cudaFuncSetAttribute(hv_bitmap_kernel<T, VEC, G, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    }
+    const int sm2 = kStageWords * sizeof(uint32_t);
+    cudaFuncSetAttribute(hv_block_kernel<T, VEC, G, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(hv_block_kernel<T, VEC, G, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(hv_block_kernel<T, VEC, G, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    configured_smem = int(smem);
   }
   a.L = c->idx.B;
   timing_begin(c, 0);
-  hv_block_kernel<T, VEC, G, false, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+  if (bitmap)
+    hv_bitmap_kernel<T, VEC, G, false, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+  else
+    hv_block_kernel<T, VEC, G, false, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
   MCD_LAUNCHED(c);
   timing_end(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   a.L = c->idx.A;
   timing_begin(c, 1);
-  if (partials)
-    hv_block_kernel<T, VEC, G, true, true><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
-  else
-    hv_block_kernel<T, VEC, G, true, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+  if (bitmap) {
+    if (partials)
+      hv_bitmap_kernel<T, VEC, G, true, true><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+    else
+      hv_bitmap_kernel<T, VEC, G, true, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+  } else {
+    if (partials)
+      hv_block_kernel<T, VEC, G, true, true><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+    else
+      hv_block_kernel<T, VEC, G, true, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+  }
   MCD_LAUNCHED(c);
   timing_end(c);
   return cudaGetLastError();

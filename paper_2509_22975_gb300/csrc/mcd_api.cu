@@ -134,7 +134,7 @@ int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
   if (!c) return MCD_E_INVALID;
   switch (option) {
     case MCD_OPT_HV_ALGO:
-      if (value != 0 && value != 1) return fail(c, MCD_E_INVALID, "HV_ALGO must be 0 or 1");
+      if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "HV_ALGO must be 0, 1 or 2");
       c->hv_algo = int(value);
       return MCD_OK;
     case MCD_OPT_KERNEL_TIMING:

@@ -110,18 +110,29 @@ def test_diagonal(which, request):
     assert np.array_equal(d.cpu().numpy(), P.diag)   # integer-valued here: exact
 
 
+@pytest.fixture(params=[pkg.HV_AUTO, pkg.HV_SEARCH], ids=["bitmap", "search"])
+def algo(request):
+    return request.param
+
+
+def with_algo(ctx, algo):
+    ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, algo)
+
+
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 @pytest.mark.parametrize("ncols", [1, 3, 8, 24, 48])
-def test_apply_ring8(ring8, dtype, ncols):
+def test_apply_ring8(ring8, dtype, ncols, algo):
     w, ctx, B, P = ring8
+    with_algo(ctx, algo)
     check_apply(ctx, P, w.lat.t, ncols, dtype, seed=ncols)
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 @pytest.mark.parametrize("ncols,ld,offset", [(1, 1, 0), (12, 12, 0), (24, 24, 0), (5, 8, 0),
                                              (4, 4, 1), (130, 132, 0)])
-def test_apply_tilted12(tilted12, dtype, ncols, ld, offset):
+def test_apply_tilted12(tilted12, dtype, ncols, ld, offset, algo):
     w, ctx, B, P = tilted12
+    with_algo(ctx, algo)
     check_apply(ctx, P, w.lat.t, ncols, dtype, ld=ld, offset=offset, seed=7 + ncols)
 
 
@@ -145,14 +156,28 @@ def test_plain_kernel_variant(tilted12, dtype):
     try:
         check_apply(ctx, P, w.lat.t, 2, dtype, seed=99)
     finally:
-        ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, 0)
+        ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, pkg.HV_AUTO)
 
 
-def test_single_state_basis():
+def test_single_state_basis(algo):
     w = C.ring8_u4()
     ctx = device_ctx(w, basis=np.array([w.seed_word()], dtype=np.uint64))
+    with_algo(ctx, algo)
     P = H.build(model(w), np.array([w.seed_word()], dtype=np.uint64))
     check_apply(ctx, P, w.lat.t, 3, np.float64)
+
+
+def test_tiny_lattice_small_bitmap(algo):
+    # 3 sites: the bitmap has fewer than 32 bits
+    lat = L.ring(3)
+    w = C.Workload("ring3", lat, 2.0, 1, 2, 0, 0.5)
+    B = fock.sector(3, 1, 2)
+    ctx = device_ctx(w, basis=B)
+    with_algo(ctx, algo)
+    P = H.build(model(w), B)
+    for dt in (np.float64, np.float32):
+        check_apply(ctx, P, lat.t, 1, dt)
+        check_apply(ctx, P, lat.t, 2, dt)
 
 
 def test_oversized_block_uses_global_search():
@@ -169,9 +194,12 @@ def test_oversized_block_uses_global_search():
     B = np.unique(np.concatenate([big] + others))
     ctx = device_ctx(w, basis=B)
     P = H.build(model(w), B)
-    for dt in (np.float64, np.float32):
-        check_apply(ctx, P, lat.t, 1, dt)
-        check_apply(ctx, P, lat.t, 6, dt)
+    for algo in (pkg.HV_AUTO, pkg.HV_SEARCH):
+        with_algo(ctx, algo)
+        for dt in (np.float64, np.float32):
+            check_apply(ctx, P, lat.t, 1, dt)
+            check_apply(ctx, P, lat.t, 6, dt)
+            check_apply(ctx, P, lat.t, 33, dt)
 
 
 def test_thirty_two_sites_random_hoppings_and_site_terms():

@@ -88,11 +88,11 @@ def test_deterministic_and_plain_variant_agree():
     a2, b2 = ctx.mcd_lanczos_coeffs()
     assert r1["iters"] == r2["iters"] == 60
     assert np.array_equal(a1, a2) and np.array_equal(b1, b2)      # bit-identical reruns
-    ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, 1)
-    r3 = ctx.mcd_lanczos_ground(400, 1e-12, 5, pkg.MCD_F64)
-    ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, 0)
-    r4 = ctx.mcd_lanczos_ground(400, 1e-12, 5, pkg.MCD_F64)
-    assert abs(r3["E0"] - r4["E0"]) < 1e-10 * abs(r4["E0"])
+    Es = []
+    for algo in (pkg.HV_PLAIN, pkg.HV_SEARCH, pkg.HV_AUTO):
+        ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, algo)
+        Es.append(ctx.mcd_lanczos_ground(400, 1e-12, 5, pkg.MCD_F64)["E0"])
+    assert max(Es) - min(Es) < 1e-10 * abs(Es[-1])
 
 
 def test_single_state_breakdown():
@@ -113,7 +113,7 @@ def test_argument_errors():
     with pytest.raises(pkg.MCDError):
         ctx.mcd_lanczos_ground(10, 1e-10, 0, 5)
     r = ctx.mcd_lanczos_ground(3, 1e-14, 0, pkg.MCD_F64, allow_not_converged=True)
-    assert r["status"] == pkg.MCDError(0, "").status or r["status"] in (0, -5)
+    assert r["status"] in (0, -5)
 
 
 @pytest.mark.slow
