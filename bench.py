@@ -202,6 +202,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--hv-cols", type=int, nargs="*", default=[1, 24])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -310,6 +311,31 @@ def main():
            "basis": {"n_states": n, "nnz_offdiag": nnz, "n_up_blocks": info["n_up_blocks"],
                      "n_dn_blocks": info["n_dn_blocks"], "sampler_s": t_sample},
            "E0_fp32": r32["E0"], "lanczos_iters_per_s_fp32": r32["iters"] / (ms * 1e-3)}
+
+    if args.hv_cols:
+        # H~V with L columns (the band-Lanczos product), fp32, timed alone with
+        # CUDA events; x, y of 1e7 x L fp32 are far larger than L2
+        hv = {}
+        for L_ in args.hv_cols:
+            x = torch.randn(n, L_, dtype=torch.float32, device=dev)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                ctx.mcd_apply(x, y)
+            torch.cuda.synchronize()
+            reps = 10
+            h0e, h1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h0e.record()
+            for _ in range(reps):
+                ctx.mcd_apply(x, y)
+            h1e.record()
+            torch.cuda.synchronize()
+            t_ms = h0e.elapsed_time(h1e) / reps
+            bytes_ = n * (8 + 2 * L_ * 4)
+            hv[f"L{L_}"] = {"ms": t_ms, "Gconn_per_s": nnz * L_ / (t_ms * 1e-3) / 1e9,
+                            "algorithmic_GBps": bytes_ / (t_ms * 1e-3) / 1e9,
+                            "frac_of_peak": bytes_ / (t_ms * 1e-3) / 1e9 / peak}
+            del x, y
+        out["hv_apply_fp32"] = hv
 
     if not args.no_fp64:
         # fp64 form and the plain fp64 path (global binary search kernel), same 200 steps

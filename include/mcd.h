@@ -155,10 +155,16 @@ int mcd_connections_noalloc(mcd_ctx* ctx, int64_t* rows_dev, int64_t* cols_dev, 
  * eigenproblem in fp64.  Stops when the residual estimate b_{m} |s_{m-1}|
  * < tol * max(1, |E0|), on an invariant subspace (b < 1e-14 scale), or at
  * max_iter (then MCD_E_NOT_CONVERGED unless tol <= 0, which asks for exactly
- * max_iter steps).  psi_dev (nullable): device [n_states] of dtype; receives
- * the normalised Ritz vector sum_n |n><n|Omega_eff> (change-of-basis Eq. of
- * App. B) by a second pass that regenerates the Krylov vectors; *residual is
- * then |H~ psi - E0 psi|, else the estimate.  E0, iters, residual: host. */
+ * max_iter steps).  The Krylov vectors are kept in device memory when they
+ * fit in half of it (else regenerated by a second pass) to form the Ritz
+ * vector sum_n |n><n|Omega_eff> (change-of-basis Eq. of App. B) in fp64.
+ * dtype MCD_F64: E0 = lowest Ritz value.  dtype MCD_F32: E0 = the fp64
+ * Rayleigh quotient <psi|H~|psi>/<psi|psi> of that Ritz vector (fp64 H~
+ * product), which removes the fp32 recursion's error to first order.
+ * psi_dev (nullable): device [n_states] of dtype, receives the normalised
+ * Ritz vector.  *residual = |H~ psi - E0 psi| / |psi| when the Ritz vector was
+ * formed (fp32 always, fp64 with psi_dev), else the estimate.  E0, iters,
+ * residual: host. */
 int mcd_lanczos_ground(mcd_ctx* ctx, int max_iter, double tol, uint64_t seed, int dtype,
                        double* E0, void* psi_dev, int* iters, double* residual);
 

@@ -27,6 +27,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kBitmapMaxSites = 16;            // 2^16-bit bitmap = 8 KiB of shared memory
 constexpr int kStageXBytes = 52 * 1024;        // x staging area of the bitmap kernel
+constexpr int kStageX1Bytes = 20 * 1024;       // x staging area of the single-column kernel
 
 struct HvArgs {
   const void* x;
@@ -43,6 +44,7 @@ struct HvArgs {
   int nw;                 // bitmap words = max(1, 2^n_sites / 32)
   int off_bm, off_pre, off_xs;
   int xs_cap;             // elements of T that fit in the x staging area
+  int off_pt;             // single-column kernel: partner table
   int ncp;                // staged row stride: ncols rounded up to VEC
 };
 
@@ -561,6 +563,253 @@ __global__ void __launch_bounds__(kThreads) hv_bitmap_kernel(const HvArgs a, con
 }
 
 // ---------------------------------------------------------------------------------
+// Single-column variant of the bitmap kernel (the Lanczos case), one thread per
+// state.  Shared memory holds, per block, a 2^n-bit bitmap of its minor words
+// packed with per-word prefix counts (uint2: bits, block-local index of the
+// first state in the word), so one 8-byte load answers "is m2 in the block"
+// and "where".  Active hops are enumerated from partner classes: for class c,
+// (m ^ P_c(m)) & first_c marks its active bonds (P_c = bit permutation taken
+// from two byte tables); two classes form one 32-bit mask whose bits are
+// taken two at a time, so each thread keeps two independent lookups in
+// flight.  Without partner classes every bond is tested in turn.
+template <typename T>
+struct L1Smem {
+  const uint2* bm;              // [nw] bits, first local index
+  const T* xs;                  // staged x of the block
+  const uint2* ptab;            // [groups][2][256] P contributions, four classes per entry
+  const uint2* pflip;           // [n_pcls * 16] (flip, between) by class and first endpoint
+  const float* dhi;
+  const float* dlo;
+  const double* d64;
+};
+
+template <typename T, bool STAGED, bool PASS_A>
+__device__ __forceinline__ T l1_fetch(const HvArgs& a, const Layout& L, const L1Smem<T>& S, int bs, int q) {
+  if (STAGED) return S.xs[q];
+  const T* x = static_cast<const T*>(a.x);
+  return __ldg(x + (PASS_A ? int64_t(bs + q) : int64_t(L.perm[bs + q])) * a.ld);
+}
+
+// block-local index of m2, or -1
+__device__ __forceinline__ int l1_find(const uint2* bm, uint32_t m2) {
+  const uint2 w = bm[m2 >> 5];
+  const uint32_t sh = m2 & 31u;
+  return ((w.x >> sh) & 1u) ? int(w.y) + __popc(w.x & ((1u << sh) - 1u)) : -1;
+}
+
+template <typename T, bool PASS_A, bool DOT, bool STAGED, bool PARTNER>
+__device__ __forceinline__ void l1_state(const HvArgs& a, const HamParams& hp, const Layout& L,
+                                         const L1Smem<T>& S, uint32_t major, int bs, int k, double& dot_acc) {
+  T* __restrict__ y = static_cast<T*>(a.y);
+  const uint32_t m = L.minor[k];
+  Acc<T> acc;
+  acc.zero();
+  if (PARTNER) {
+    const uint32_t mm = m | (m << 16);
+    for (int g = 0; 4 * g < hp.n_pcls; ++g) {
+      const uint2 t0 = S.ptab[g * 512 + (m & 255u)];
+      const uint2 t1 = S.ptab[g * 512 + 256 + (m >> 8)];
+      for (int h = 0; h < 2; ++h) {
+        const int c = 4 * g + 2 * h;
+        if (c >= hp.n_pcls) break;
+        const bool pair = c + 1 < hp.n_pcls;
+        const uint32_t pp = h ? (t0.y | t1.y) : (t0.x | t1.x);
+        uint32_t act = (mm ^ pp) & (hp.pfirst[c] | (pair ? hp.pfirst[c + 1] << 16 : 0u));
+        const uint2* fl = S.pflip + c * 16;   // bit position p -> class c + (p >> 4), site p & 15
+        T s0 = T(0), s1 = T(0);
+        while (act) {
+          const int i1 = __ffs(act) - 1;
+          act &= act - 1u;
+          const bool two = act != 0u;
+          const int i2 = two ? __ffs(act) - 1 : i1;
+          act &= act - 1u;   // no-op when act == 0
+          const uint2 f1 = fl[i1];
+          const uint2 f2 = fl[i2];
+          const int q1 = l1_find(S.bm, m ^ f1.x);
+          const int q2 = two ? l1_find(S.bm, m ^ f2.x) : -1;
+          if (q1 >= 0) {
+            T xv = l1_fetch<T, STAGED, PASS_A>(a, L, S, bs, q1);
+            if (__popc(m & f1.y) & 1u) xv = -xv;
+            if (i1 >> 4) s1 += xv; else s0 += xv;
+          }
+          if (q2 >= 0) {
+            T xv = l1_fetch<T, STAGED, PASS_A>(a, L, S, bs, q2);
+            if (__popc(m & f2.y) & 1u) xv = -xv;
+            if (i2 >> 4) s1 += xv; else s0 += xv;
+          }
+        }
+        if (sizeof(T) == 4) {
+          acc.fma(T(hp.pcls_hi[c]), T(hp.pcls_lo[c]), s0);
+          if (pair) acc.fma(T(hp.pcls_hi[c + 1]), T(hp.pcls_lo[c + 1]), s1);
+        } else {
+          acc.fma(T(hp.pcls_t[c]), T(0), s0);
+          if (pair) acc.fma(T(hp.pcls_t[c + 1]), T(0), s1);
+        }
+      }
+    }
+  } else {
+    int b = 0;
+    for (int c = 0; c < hp.n_class; ++c) {
+      const int e = hp.cls_end[c];
+      T s = T(0);
+      for (; b < e; ++b) {
+        const uint32_t mk = hp.bonds[b].mask;
+        if (__popc(m & mk) != 1) continue;
+        const int q = l1_find(S.bm, m ^ mk);
+        if (q < 0) continue;
+        T xv = l1_fetch<T, STAGED, PASS_A>(a, L, S, bs, q);
+        s += (__popc(m & hp.bonds[b].between) & 1u) ? -xv : xv;
+      }
+      if (sizeof(T) == 4) acc.fma(T(hp.cls_hi[c]), T(hp.cls_lo[c]), s);
+      else acc.fma(T(hp.cls_t[c]), T(0), s);
+    }
+  }
+  if (PASS_A) {
+    const T* x = static_cast<const T*>(a.x);
+    const T xk = STAGED ? S.xs[k - bs] : __ldg(x + int64_t(k) * a.ld);
+    const int nu = __popc(major & m);
+    if (hp.uniform) {
+      if (sizeof(T) == 4) acc.fma(T(S.dhi[nu]), T(S.dlo[nu]), xk);
+      else acc.fma(T(S.d64[nu]), T(0), xk);
+    } else {
+      const Coef<T> dc = diag_coef<T>(hp, major, m);
+      acc.fma(dc.hi, dc.lo, xk);
+    }
+    const T out = acc.value() + y[int64_t(k) * a.ld];
+    y[int64_t(k) * a.ld] = out;
+    if (DOT) dot_acc += double(xk) * double(out);
+  } else {
+    y[int64_t(L.perm[k]) * a.ld] = acc.value();
+  }
+}
+
+template <typename T, bool PASS_A, bool DOT>
+__global__ void __launch_bounds__(kThreads) hv_l1_kernel(const HvArgs a, const HamParams hp) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __shared__ uint32_t s_b0, s_b1;
+  __shared__ double s_red[kThreads / 32];
+  __shared__ float s_dhi[kMaxSites + 1], s_dlo[kMaxSites + 1];
+  __shared__ double s_d64[kMaxSites + 1];
+  uint2* s_pt = reinterpret_cast<uint2*>(s_dyn + a.off_pt);
+  uint2* bm = reinterpret_cast<uint2*>(s_dyn + a.off_bm);
+  T* xs = reinterpret_cast<T*>(s_dyn + a.off_xs);
+  const bool use_p = hp.n_pcls > 0;
+
+  const Layout& L = a.L;
+  const int item = blockIdx.x;
+  const int64_t k0 = int64_t(item) * kItem;
+  const int64_t k1 = (k0 + kItem < L.n) ? k0 + kItem : L.n;
+  for (int i = threadIdx.x; i < a.nw; i += kThreads) bm[i] = make_uint2(0u, 0u);
+  if (use_p)   // P table groups followed by the (flip, between) table, contiguous in global memory
+    for (int i = threadIdx.x; i < ((hp.n_pcls + 3) / 4) * 512 + hp.n_pcls * 16; i += kThreads) s_pt[i] = hp.ptab[i];
+  if (threadIdx.x <= kMaxSites) {
+    s_dhi[threadIdx.x] = hp.dtab_hi[threadIdx.x];
+    s_dlo[threadIdx.x] = hp.dtab_lo[threadIdx.x];
+    s_d64[threadIdx.x] = hp.dtab[threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    const uint32_t b0 = L.item_blk[item];
+    uint32_t b1 = L.item_blk[item + 1];
+    if (b1 == uint32_t(L.nblk) || L.blk_off[b1] == uint32_t(k1)) b1 -= 1;
+    s_b0 = b0;
+    s_b1 = b1;
+  }
+  __syncthreads();
+  const uint32_t b0 = s_b0, b1 = s_b1;
+  const T* __restrict__ x = static_cast<const T*>(a.x);
+  L1Smem<T> S{bm, xs, s_pt, s_pt + ((hp.n_pcls + 3) / 4) * 512, s_dhi, s_dlo, s_d64};
+  double dot_acc = 0.0;
+
+  for (uint32_t blk = b0; blk <= b1; ++blk) {
+    const int bs = int(L.blk_off[blk]), be = int(L.blk_off[blk + 1]);
+    const uint32_t major = L.blk_major[blk];
+    const int bsz = be - bs;
+    const bool staged = bsz <= a.xs_cap;
+    // build: loads of four states are issued before any of them is used
+    for (int q0 = threadIdx.x; q0 < bsz; q0 += 4 * kThreads) {
+      uint32_t d[4], dp[4];
+      T xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * kThreads;
+        d[u] = q < bsz ? __ldg(L.minor + bs + q) : 0u;
+        dp[u] = (q < bsz && q > 0) ? __ldg(L.minor + bs + q - 1) : 0xFFFFFFFFu;
+      }
+      if (staged) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + u * kThreads;
+          xv[u] = q < bsz ? __ldg(x + (PASS_A ? int64_t(bs + q) : int64_t(__ldg(L.perm + bs + q))) * a.ld) : T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * kThreads;
+        if (q < bsz) {
+          atomicOr(&bm[d[u] >> 5].x, 1u << (d[u] & 31));
+          if (q == 0 || (dp[u] >> 5) != (d[u] >> 5)) bm[d[u] >> 5].y = uint32_t(q);
+          if (staged) xs[q] = xv[u];
+        }
+      }
+    }
+    __syncthreads();
+    const int lo = (int64_t(bs) > k0) ? bs : int(k0);
+    const int hi = (int64_t(be) < k1) ? be : int(k1);
+    if (use_p) {
+      if (staged) {
+        for (int k = lo + threadIdx.x; k < hi; k += kThreads)
+          l1_state<T, PASS_A, DOT, true, true>(a, hp, L, S, major, bs, k, dot_acc);
+      } else {
+        for (int k = lo + threadIdx.x; k < hi; k += kThreads)
+          l1_state<T, PASS_A, DOT, false, true>(a, hp, L, S, major, bs, k, dot_acc);
+      }
+    } else if (staged) {
+      for (int k = lo + threadIdx.x; k < hi; k += kThreads)
+        l1_state<T, PASS_A, DOT, true, false>(a, hp, L, S, major, bs, k, dot_acc);
+    } else {
+      for (int k = lo + threadIdx.x; k < hi; k += kThreads)
+        l1_state<T, PASS_A, DOT, false, false>(a, hp, L, S, major, bs, k, dot_acc);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < bsz; q += kThreads) bm[L.minor[bs + q] >> 5].x = 0u;
+    __syncthreads();
+  }
+
+  if (DOT) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot_acc += __shfl_xor_sync(0xffffffffu, dot_acc, o);
+    if (lane == 0) s_red[threadIdx.x >> 5] = dot_acc;
+    __syncthreads();
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
+      a.dot_partials[blockIdx.x] = sum;
+      __threadfence();
+      const unsigned t = atomicAdd(a.ticket, 1u);
+      s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+      double sum = 0.0;
+      for (int i = threadIdx.x; i < int(gridDim.x); i += kThreads) sum += __ldcg(a.dot_partials + i);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      __syncthreads();
+      if (lane == 0) s_red[threadIdx.x >> 5] = sum;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) tot += s_red[w];
+        *a.dot_out = tot;
+        *a.ticket = 0u;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // Plain path: one thread per state, both spins, binary search over the whole
 // sorted basis in global memory.  Kept as the simple reference GPU path.
 template <typename T>
@@ -711,6 +960,39 @@ cudaError_t launch_pair(mcd_ctx* c, const void* x, void* y, int ncols, int ld, d
     cudaFuncSetAttribute(hv_block_kernel<T, VEC, G, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
     cudaFuncSetAttribute(hv_block_kernel<T, VEC, G, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
     configured_smem = int(smem);
+  }
+  const bool l1 = bitmap && G == 1 && VEC == 1 && ncols == 1 && (c->hp->n_class > 0 || c->hp->n_bonds == 0);
+  if (l1) {
+    // layout: [ptab: groups x 512 uint2][bm: nw uint2][xs]
+    const int ng = (c->hp->n_pcls + 3) / 4;
+    a.off_pt = 0;
+    a.off_bm = (ng * 512 + c->hp->n_pcls * 16) * 8;
+    a.off_xs = (a.off_bm + 8 * a.nw + 15) & ~15;
+    smem = size_t(a.off_xs) + kStageX1Bytes;
+    a.xs_cap = int(kStageX1Bytes / sizeof(T));
+    static int configured_l1 = -1;
+    if (configured_l1 < int(smem)) {
+      cudaFuncSetAttribute(hv_l1_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      cudaFuncSetAttribute(hv_l1_kernel<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      cudaFuncSetAttribute(hv_l1_kernel<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      configured_l1 = int(smem);
+    }
+    a.L = c->idx.B;
+    timing_begin(c, 0);
+    hv_l1_kernel<T, false, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+    MCD_LAUNCHED(c);
+    timing_end(c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    a.L = c->idx.A;
+    timing_begin(c, 1);
+    if (partials)
+      hv_l1_kernel<T, true, true><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+    else
+      hv_l1_kernel<T, true, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+    MCD_LAUNCHED(c);
+    timing_end(c);
+    return cudaGetLastError();
   }
   a.L = c->idx.B;
   timing_begin(c, 0);

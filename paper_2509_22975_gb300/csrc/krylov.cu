@@ -129,8 +129,9 @@ __global__ void __launch_bounds__(kThreads) start_kernel(T* s0, int64_t n, uint6
 // s_next = al * w + be * s + ga * s_prev (written over s_prev), nrm2 reduced.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) update_kernel(const T* __restrict__ w, const T* __restrict__ s,
-                                                          T* s_prev, int64_t n, int step, const double* scal,
-                                                          Slots sl, double* partials, unsigned int* ticket) {
+                                                          const T* s_prev, T* out, int64_t n, int step,
+                                                          const double* scal, Slots sl, double* partials,
+                                                          unsigned int* ticket) {
   __shared__ T c_al, c_be, c_ga;
   __shared__ int s_use_prev;
   if (threadIdx.x == 0) {
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const T* __restrict__ 
     if (use_prev) ld(s_prev + q * W, c);
 #pragma unroll
     for (int i = 0; i < W; ++i) o[i] = use_prev ? (al * a[i] + be * b[i] + ga * c[i]) : (al * a[i] + be * b[i]);
-    st(s_prev + q * W, o);
+    st(out + q * W, o);
     acc += sumsq<T, W>(o);
   }
   // tail
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const T* __restrict__ 
     for (int64_t k = nv * W + threadIdx.x; k < n; k += kThreads) {
       T o = al * w[k] + be * s[k];
       if (use_prev) o += ga * s_prev[k];
-      s_prev[k] = o;
+      out[k] = o;
       acc += double(o) * double(o);
     }
   }
@@ -178,6 +179,30 @@ __global__ void axpy_kernel(T* psi, const T* s, int64_t n, double coef) {
   const T c = T(coef);
   for (int64_t k = int64_t(blockIdx.x) * kThreads + threadIdx.x; k < n; k += int64_t(gridDim.x) * kThreads)
     psi[k] += c * s[k];
+}
+
+// psi[k] = sum_{j < m} coef[j] V[j][k] in fp64 (V: m stored vectors of n)
+template <typename T>
+__global__ void combine_kernel(double* psi, const T* V, int64_t n, int m, const double* coef) {
+  for (int64_t k = int64_t(blockIdx.x) * kThreads + threadIdx.x; k < n; k += int64_t(gridDim.x) * kThreads) {
+    double acc = 0.0;
+    for (int j = 0; j < m; ++j) acc = fma(__ldg(coef + j), double(V[int64_t(j) * n + k]), acc);
+    psi[k] = acc;
+  }
+}
+
+// psi64 += coef * double(s)
+template <typename T>
+__global__ void axpy64_kernel(double* psi, const T* s, int64_t n, double coef) {
+  for (int64_t k = int64_t(blockIdx.x) * kThreads + threadIdx.x; k < n; k += int64_t(gridDim.x) * kThreads)
+    psi[k] = fma(coef, double(s[k]), psi[k]);
+}
+
+// out[k] = T(v[k] * f)
+template <typename T>
+__global__ void cast_scale_kernel(T* out, const double* v, int64_t n, double f) {
+  for (int64_t k = int64_t(blockIdx.x) * kThreads + threadIdx.x; k < n; k += int64_t(gridDim.x) * kThreads)
+    out[k] = T(v[k] * f);
 }
 
 // out = sum_k a[k] b[k] (or sum a^2 when b == nullptr)
@@ -220,10 +245,22 @@ int ensure_work(mcd_ctx* c, int dtype, int max_iter) {
   const size_t es = dtype == MCD_F64 ? 8 : 4;
   const int cap = max_iter + 2;
   const int ctas = std::max<int>(int(c->idx.A.n_items), 152 * 8) + 8;
-  if (w.n == n && w.dtype == dtype && w.scal_cap >= cap && w.max_ctas >= ctas) return MCD_OK;
+  // keep every Krylov vector when it fits in half of the free memory (no
+  // second pass for the Ritz vector); else two rotating slots
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const size_t held = w.V ? size_t(w.nvec) * size_t(w.n) * (w.dtype == MCD_F64 ? 8 : 4) : 0;
+  const bool want_store = double(max_iter + 1) * double(n) * double(es) <= 0.5 * double(free_b + held);
+  const int nvec = want_store ? max_iter + 1 : 2;
+  if (w.n == n && w.dtype == dtype && w.scal_cap >= cap && w.max_ctas >= ctas && w.nvec >= nvec &&
+      w.stored == want_store)
+    return MCD_OK;
   free_lanczos(w);
-  cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&w.v[i], size_t(n) * es + 64);
+  cudaError_t e = cudaMalloc(&w.W, size_t(n) * es + 64);
+  if (e == cudaSuccess) e = cudaMalloc(&w.V, size_t(nvec) * size_t(n) * es + 64);
+  if (e == cudaSuccess && dtype == MCD_F32) e = cudaMalloc(&w.psi64, size_t(n) * 8 + 64);
+  if (e == cudaSuccess && dtype == MCD_F32) e = cudaMalloc(&w.w64, size_t(n) * 8 + 64);
+  if (e == cudaSuccess) e = cudaMalloc(&w.coef, sizeof(double) * cap);
   if (e == cudaSuccess) e = cudaMalloc(&w.scal, sizeof(double) * (2 * cap + 16));
   if (e == cudaSuccess) e = cudaMalloc(&w.partials, sizeof(double) * ctas);
   if (e == cudaSuccess) e = cudaMalloc(&w.ticket, sizeof(unsigned int));
@@ -234,6 +271,8 @@ int ensure_work(mcd_ctx* c, int dtype, int max_iter) {
   }
   w.n = n;
   w.dtype = dtype;
+  w.nvec = nvec;
+  w.stored = want_store;
   w.scal_cap = cap;
   w.max_ctas = ctas;
   return MCD_OK;
@@ -248,36 +287,34 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
   const Slots sl{w.scal_cap};
   const int vg = vec_grid(n);
   const uint64_t key = smix(smix(seed + kGamma) ^ 0x4C414E43ull);   // stream "LANC"
-  T* buf[3] = {static_cast<T*>(w.v[0]), static_cast<T*>(w.v[1]), static_cast<T*>(w.v[2])};
+  T* V = static_cast<T*>(w.V);
+  T* W = static_cast<T*>(w.W);
+  const bool fp32 = sizeof(T) == 4;
+  // Krylov vector s_j: its own slot when all are stored, else slot j % 2
+  auto vec = [&](int j) -> T* { return V + int64_t(w.stored ? j : (j & 1)) * n; };
 
   auto fresh_start = [&]() -> cudaError_t {
-    start_kernel<T><<<vg, kThreads, 0, s>>>(buf[0], n, key, w.partials, w.ticket, w.scal + sl.nrm2(0));
+    start_kernel<T><<<vg, kThreads, 0, s>>>(vec(0), n, key, w.partials, w.ticket, w.scal + sl.nrm2(0));
     MCD_LAUNCHED(c);
     return cudaGetLastError();
   };
-  // one step: C -> W = H C (dot into slot), P <- s_{n+1}
-  auto step = [&](int it, T*& P, T*& C, T* W) -> int {
-    int st = hv_apply(c, C, W, 1, 1, sizeof(T) == 8 ? MCD_F64 : MCD_F32, w.partials, sl.dot(it));
+  // one step: W = H s_it (fused <s_it, W> into slot dot(it)), s_{it+1} from W, s_it, s_{it-1}
+  auto step = [&](int it) -> int {
+    int st = hv_apply(c, vec(it), W, 1, 1, fp32 ? MCD_F32 : MCD_F64, w.partials, sl.dot(it));
     if (st != MCD_OK) return st;
     timing_begin(c, 2);
-    update_kernel<T><<<vg, kThreads, 0, s>>>(W, C, P, n, it, w.scal, sl, w.partials, w.ticket);
+    update_kernel<T><<<vg, kThreads, 0, s>>>(W, vec(it), vec(it > 0 ? it - 1 : 0), vec(it + 1), n, it, w.scal,
+                                             sl, w.partials, w.ticket);
     MCD_LAUNCHED(c);
     timing_end(c);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(c, e, "Lanczos update");
-    T* t = P;
-    P = C;
-    C = t;
-    return MCD_OK;
+    return e == cudaSuccess ? MCD_OK : cuda_fail(c, e, "Lanczos update");
   };
 
   cudaError_t e = fresh_start();
   if (e != cudaSuccess) return cuda_fail(c, e, "Lanczos start");
-  T* P = buf[1];
-  T* C = buf[0];
-  T* W = buf[2];
   std::vector<double> nrm2, dot;
-  std::vector<double> a, b, vec;
+  std::vector<double> a, b, ev;
   double E0 = 0.0, resid = INFINITY;
   int m = 0;          // completed steps
   bool done = false, breakdown = false, bad = false;
@@ -285,7 +322,7 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
   while (!done && m < max_iter) {
     const int todo = std::min(chunk, max_iter - m);
     for (int k = 0; k < todo; ++k) {
-      int st = step(m + k, P, C, W);
+      int st = step(m + k);
       if (st != MCD_OK) return st;
     }
     m += todo;
@@ -318,9 +355,9 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
       }
     }
     if (mm == 0) return fail(c, MCD_E_BREAKDOWN, "Lanczos: non-finite first coefficient");
-    vec.assign(mm, 0.0);
-    E0 = tridiag_lowest(a.data(), b.data(), mm, vec.data());
-    resid = (breakdown ? 0.0 : b[mm]) * std::fabs(vec[mm - 1]);
+    ev.assign(mm, 0.0);
+    E0 = tridiag_lowest(a.data(), b.data(), mm, ev.data());
+    resid = (breakdown ? 0.0 : b[mm]) * std::fabs(ev[mm - 1]);
     m = mm;
     if (breakdown || bad) done = true;
     else if (tol > 0 && resid < tol * std::max(1.0, std::fabs(E0))) done = true;
@@ -333,40 +370,64 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
   if (bad && !breakdown) return fail(c, MCD_E_BREAKDOWN, "Lanczos: non-finite coefficient");
   int status = MCD_OK;
   if (!done && tol > 0) status = MCD_E_NOT_CONVERGED;
+  if (!psi && !fp32) return status;
 
-  if (psi) {
-    // second pass: regenerate s_0..s_{m-1}; psi = sum c_k sig_k s_k
-    e = cudaMemsetAsync(psi, 0, sizeof(T) * n, s);
+  // Ritz vector sum_k ev[k] sig_k s_k (change-of-basis Eq. of App. B), in fp64
+  // for the fp32 form (whose E0 is then the fp64 Rayleigh quotient of it)
+  std::vector<double> coef(m);
+  for (int k = 0; k < m; ++k) coef[k] = ev[k] / std::sqrt(nrm2[k]);
+  double* p64 = fp32 ? w.psi64 : reinterpret_cast<double*>(psi);
+  if (w.stored) {
+    e = cudaMemcpyAsync(w.coef, coef.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Ritz coefficients");
+    if (fp32 || sizeof(T) == 8) {
+      combine_kernel<T><<<vg, kThreads, 0, s>>>(p64, V, n, m, w.coef);
+      MCD_LAUNCHED(c);
+    }
+  } else {
+    e = cudaMemsetAsync(p64, 0, sizeof(double) * n, s);
     if (e == cudaSuccess) e = fresh_start();
     if (e != cudaSuccess) return cuda_fail(c, e, "Ritz vector");
-    P = buf[1];
-    C = buf[0];
     for (int k = 0; k < m; ++k) {
-      const double sig = 1.0 / std::sqrt(nrm2[k]);
-      axpy_kernel<T><<<vg, kThreads, 0, s>>>(psi, C, n, vec[k] * sig);
+      axpy64_kernel<T><<<vg, kThreads, 0, s>>>(p64, vec(k), n, coef[k]);
       MCD_LAUNCHED(c);
       if (k + 1 < m) {
-        int st = step(k, P, C, W);
+        int st = step(k);
         if (st != MCD_OK) return st;
       }
     }
-    // normalise, then |H psi - E0 psi|
-    double nn = 0.0, rr = 0.0;
-    dot_kernel<T><<<vg, kThreads, 0, s>>>(psi, nullptr, n, w.partials, w.ticket, w.scal + sl.misc(0));
+  }
+  // |psi|^2, <psi, H psi>, |H psi - E psi|^2 in fp64
+  double* hp64 = fp32 ? w.w64 : reinterpret_cast<double*>(W);
+  double nn = 0.0, hh = 0.0, rr = 0.0;
+  int st = hv_apply(c, p64, hp64, 1, 1, MCD_F64, nullptr, 0);
+  if (st != MCD_OK) return st;
+  dot_kernel<double><<<vg, kThreads, 0, s>>>(p64, nullptr, n, w.partials, w.ticket, w.scal + sl.misc(0));
+  MCD_LAUNCHED(c);
+  dot_kernel<double><<<vg, kThreads, 0, s>>>(p64, hp64, n, w.partials, w.ticket, w.scal + sl.misc(1));
+  MCD_LAUNCHED(c);
+  e = cudaMemcpyAsync(&nn, w.scal + sl.misc(0), 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hh, w.scal + sl.misc(1), 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "Ritz norm");
+  const double Eq = hh / nn;
+  if (fp32) {
+    // fp32 form: E0 = Rayleigh quotient of the Ritz vector with an fp64 H~
+    // (variational; error quadratic in the Ritz vector's error)
+    E0 = Eq;
+    *E0_out = Eq;
+  }
+  resid_kernel<double><<<vg, kThreads, 0, s>>>(hp64, p64, n, E0, w.partials, w.ticket, w.scal + sl.misc(2));
+  MCD_LAUNCHED(c);
+  e = cudaMemcpyAsync(&rr, w.scal + sl.misc(2), 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "Ritz residual");
+  *resid_out = std::sqrt(rr / nn);
+  if (psi) {
+    cast_scale_kernel<T><<<vg, kThreads, 0, s>>>(psi, p64, n, 1.0 / std::sqrt(nn));
     MCD_LAUNCHED(c);
-    e = cudaMemcpyAsync(&nn, w.scal + sl.misc(0), 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "Ritz norm");
-    scale_kernel<T><<<vg, kThreads, 0, s>>>(psi, n, 1.0 / std::sqrt(nn));
-    MCD_LAUNCHED(c);
-    int st = hv_apply(c, psi, W, 1, 1, sizeof(T) == 8 ? MCD_F64 : MCD_F32, nullptr, 0);
-    if (st != MCD_OK) return st;
-    resid_kernel<T><<<vg, kThreads, 0, s>>>(W, psi, n, E0, w.partials, w.ticket, w.scal + sl.misc(1));
-    MCD_LAUNCHED(c);
-    e = cudaMemcpyAsync(&rr, w.scal + sl.misc(1), 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "Ritz residual");
-    *resid_out = std::sqrt(rr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "Ritz output");
   }
   return status;
 }
@@ -374,10 +435,8 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
 }  // namespace
 
 void free_lanczos(LanczosWork& w) {
-  for (auto& p : w.v) {
+  for (void* p : {w.W, w.V, static_cast<void*>(w.psi64), static_cast<void*>(w.w64), static_cast<void*>(w.coef)})
     if (p) cudaFree(p);
-    p = nullptr;
-  }
   if (w.scal) cudaFree(w.scal);
   if (w.partials) cudaFree(w.partials);
   if (w.ticket) cudaFree(w.ticket);

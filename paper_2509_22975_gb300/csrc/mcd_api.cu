@@ -1,5 +1,7 @@
 // extern "C" entry points declared in include/mcd.h: argument checks, state
 // handling and dispatch to the sampler, index, H*v and Lanczos code.
+#include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -113,6 +115,7 @@ int mcd_destroy(mcd_ctx* c) {
     free_lanczos(c->lw);
     if (c->d_eps) cudaFree(c->d_eps);
     if (c->d_U) cudaFree(c->d_U);
+    if (c->d_pclass) cudaFree(c->d_pclass);
     if (c->tm) {
       if (c->tm->created)
         for (auto& ev : c->tm->ev) cudaEventDestroy(ev);
@@ -223,6 +226,32 @@ int mcd_set_hamiltonian(mcd_ctx* c, int n, const double* t, const double* eps, c
       b.t_lo = float(v - double(b.t_hi));
     }
   hp.n_bonds = nb;
+  // group bonds by amplitude (stable), so kernels can sum +-x per class and
+  // multiply by t once
+  {
+    std::vector<double> vals;
+    for (int b = 0; b < nb; ++b) {
+      bool seen = false;
+      for (double v : vals) seen |= (v == hp.bonds[b].t);
+      if (!seen) vals.push_back(hp.bonds[b].t);
+    }
+    if (int(vals.size()) <= kMaxClasses) {
+      std::vector<Bond> sorted;
+      sorted.reserve(nb);
+      hp.n_class = int(vals.size());
+      for (int cidx = 0; cidx < hp.n_class; ++cidx) {
+        for (int b = 0; b < nb; ++b)
+          if (hp.bonds[b].t == vals[cidx]) sorted.push_back(hp.bonds[b]);
+        hp.cls_end[cidx] = int(sorted.size());
+        hp.cls_t[cidx] = vals[cidx];
+        hp.cls_hi[cidx] = float(vals[cidx]);
+        hp.cls_lo[cidx] = float(vals[cidx] - double(hp.cls_hi[cidx]));
+      }
+      for (int b = 0; b < nb; ++b) hp.bonds[b] = sorted[b];
+    } else {
+      hp.n_class = 0;
+    }
+  }
   bool uniform = true;
   for (int i = 1; i < n; ++i)
     if (e[i] != e[0] || u[i] != u[0]) uniform = false;
@@ -248,6 +277,80 @@ int mcd_set_hamiltonian(mcd_ctx* c, int n, const double* t, const double* eps, c
     if (er != cudaSuccess) return cuda_fail(c, er, "copy eps, U");
     hp.eps = c->d_eps;
     hp.U = c->d_U;
+    // partner classes for the single-column kernel (n <= 16), built inside
+    // each amplitude class so that every partner class has one amplitude
+    hp.n_pcls = 0;
+    hp.ptab = nullptr;
+    if (n <= 16 && hp.n_class > 0) {
+      std::vector<std::array<int, 16>> first;   // first[c][i] = partner or -1
+      std::vector<double> amp;
+      bool ok = true;
+      int b = 0;
+      for (int ac = 0; ac < hp.n_class && ok; ++ac) {
+        const size_t c0 = first.size();
+        for (; b < hp.cls_end[ac]; ++b) {
+          const int u = __builtin_ctz(hp.bonds[b].mask);
+          const int v = 31 - __builtin_clz(hp.bonds[b].mask);
+          bool placed = false;
+          for (size_t cc = c0; cc < first.size() && !placed; ++cc) {
+            if (first[cc][u] < 0) { first[cc][u] = v; placed = true; }
+            else if (first[cc][v] < 0) { first[cc][v] = u; placed = true; }
+          }
+          if (!placed) {
+            if (int(first.size()) == kMaxPClasses) { ok = false; break; }
+            std::array<int, 16> f;
+            f.fill(-1);
+            f[u] = v;
+            first.push_back(f);
+            amp.push_back(hp.cls_t[ac]);
+          }
+        }
+      }
+      if (ok && !first.empty()) {
+        const int np = int(first.size());
+        const int ng = (np + 3) / 4;
+        std::vector<uint2> tab(size_t(ng) * 512 + size_t(np) * 16);
+        for (auto& e : tab) e = make_uint2(0u, 0u);
+        uint2* flips = tab.data() + size_t(ng) * 512;
+        for (int cc = 0; cc < np; ++cc) {
+          uint32_t fm = 0;
+          uint64_t pk = 0;
+          for (int i = 0; i < 16; ++i) {
+            const int j = first[cc][i];
+            if (j < 0) continue;
+            fm |= 1u << i;
+            pk |= uint64_t(j) << (4 * i);
+            {
+              const int lo = std::min(i, j), hi = std::max(i, j);
+              flips[size_t(cc) * 16 + i] =
+                  make_uint2((1u << i) | (1u << j), ((1u << hi) - 1u) & ~((1u << (lo + 1)) - 1u));
+            }
+            const int k = j >> 3, bit = j & 7;
+            const int g = cc / 4, slot = cc % 4;
+            for (int vv = 0; vv < 256; ++vv) {
+              if (!((vv >> bit) & 1)) continue;
+              uint2& e = tab[size_t(g) * 512 + size_t(k) * 256 + vv];
+              const uint32_t add = (1u << i) << (16 * (slot & 1));
+              if (slot < 2) e.x |= add; else e.y |= add;
+            }
+          }
+          hp.pfirst[cc] = fm;
+          hp.ppart[cc] = pk;
+          hp.pcls_t[cc] = amp[cc];
+          hp.pcls_hi[cc] = float(amp[cc]);
+          hp.pcls_lo[cc] = float(amp[cc] - double(hp.pcls_hi[cc]));
+        }
+        if (c->d_pclass) cudaFree(c->d_pclass);
+        c->d_pclass = nullptr;
+        cudaError_t er2 = cudaMalloc(&c->d_pclass, tab.size() * sizeof(uint2));
+        if (er2 == cudaSuccess)
+          er2 = cudaMemcpy(c->d_pclass, tab.data(), tab.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+        if (er2 != cudaSuccess) return cuda_fail(c, er2, "partner tables");
+        hp.ptab = static_cast<const uint2*>(c->d_pclass);
+        hp.pflip = hp.ptab + size_t(ng) * 512;
+        hp.n_pcls = np;
+      }
+    }
   }
   c->has_ham = true;
   if (sector_changed) {

@@ -16,6 +16,8 @@ constexpr int kMaxBonds = kMaxSites * (kMaxSites - 1) / 2;   // 496
 constexpr int kItem = 1024;          // states per work item of the block kernels
 constexpr int kStageWords = 12288;   // minor words a CTA stages in shared memory
 constexpr int kTimingClasses = 4;
+constexpr int kMaxClasses = 16;      // distinct hopping amplitudes handled by class sums
+constexpr int kMaxPClasses = 32;     // partner classes of the single-column kernel
 
 // One undirected bond (i < j, t_ij != 0).  A state of one spin can hop along
 // it iff exactly one of its two sites is occupied; the hop flips both bits.
@@ -37,8 +39,31 @@ struct HamParams {
   float dtab_lo[kMaxSites + 1];
   const double* eps;    // device [n] (non-uniform case)
   const double* U;      // device [n] (non-uniform case)
+  // Bonds are stored grouped by equal t_ij ("classes"): class c holds bonds
+  // [c ? cls_end[c-1] : 0, cls_end[c]).  n_class = 0 when there are more than
+  // kMaxClasses distinct amplitudes.
+  int n_class;
+  int cls_end[kMaxClasses];
+  float cls_hi[kMaxClasses], cls_lo[kMaxClasses];
+  double cls_t[kMaxClasses];
   Bond bonds[kMaxBonds];
+  // Partner classes (n_sites <= 16): the bonds of one amplitude split into
+  // classes in which every site is the first endpoint of at most one bond.
+  // For class c, P_c(m) has bit i = bit partner_c(i) of m, so
+  // (m ^ P_c(m)) & pfirst[c] marks the active bonds of c by their first
+  // endpoint.  ppart[c] packs partner_c(i) in nibble i; pcls_t* is the common
+  // amplitude of class c.  ptab (device) holds, for each group of four classes
+  // and each byte position k in {0, 1} and byte value v, the four 16-bit
+  // contributions of that byte to P_{4g..4g+3}(m), as one uint2.
+  int n_pcls;                       // 0 = not available (n_sites > 16 or too many)
+  uint32_t pfirst[kMaxPClasses];
+  uint64_t ppart[kMaxPClasses];
+  float pcls_hi[kMaxPClasses], pcls_lo[kMaxPClasses];
+  double pcls_t[kMaxPClasses];
+  const uint2* ptab;                // device [ceil(n_pcls / 4)][2][256]
+  const uint2* pflip;               // device [n_pcls][16]: (flip, between) of first endpoint i
 };
+
 
 // One of the two orderings of the basis used by the H*v kernels.
 //   up-major (A): basis order; blocks share an up word; minor = dn word.
@@ -65,7 +90,13 @@ struct DevIndex {
 struct LanczosWork {
   int64_t n = 0;
   int dtype = -1;
-  void* v[3] = {nullptr, nullptr, nullptr};   // rotating Krylov storage
+  void* W = nullptr;             // H s_n
+  void* V = nullptr;             // Krylov vectors: nvec slots of n elements
+  int nvec = 0;                  // max_iter + 1 (all stored) or 2 (rotating)
+  bool stored = false;
+  double* psi64 = nullptr;       // fp64 Ritz vector and H psi (fp32 form polish)
+  double* w64 = nullptr;
+  double* coef = nullptr;        // device Ritz coefficients
   double* scal = nullptr;        // device scalar area (see krylov.cu)
   int scal_cap = 0;
   double* partials = nullptr;    // per-CTA fp64 partial sums
@@ -95,6 +126,7 @@ struct mcd_ctx {
   mcd::HamParams* hp = nullptr;       // host copy (large struct)
   double* d_eps = nullptr;
   double* d_U = nullptr;
+  void* d_pclass = nullptr;           // partner-class tables (pt, pe)
   // Basis (host copy valid when basis_on_host; n_basis is authoritative)
   std::vector<uint64_t> basis;
   int64_t n_basis = 0;
