@@ -1,0 +1,170 @@
+"""Green function in the truncated excited subspaces (Sec. "Subspace of the
+Green function", Sec. "Further truncation", App. C).
+
+Steps, in the paper's order:
+
+1. target-weight truncation: normalise |Omega~>, order its coefficients by
+   |c_n|^2 (largest first; ties by basis index) and keep the shortest prefix
+   whose weight reaches w_t; the kept part is renormalised (reading: the paper
+   does not say whether it renormalises);
+2. excited subspaces F~+ = U_mu c^dag_mu F~ and F~- = U_mu c_mu F~ (each state
+   once), over the kept states;
+3. start vectors |phi_nu> = c^dag_nu |Omega~> in F~+ (c_nu |Omega~> in F~-);
+4. band Lanczos: an orthonormal basis of the block Krylov space
+   K_r^L = span{phi, H phi, ..., H^(r-1) phi} of r blocks, and the effective
+   matrix H_eff = V^T H V.  In exact arithmetic this is what band Lanczos
+   builds; the oracle builds it plainly (Gram-Schmidt against every earlier
+   vector, twice, dropping candidates whose norm falls below a tolerance), and
+   forms H_eff explicitly instead of relying on its band structure;
+5. the eigenpairs (E_m, S_m) of H_eff, Q_{mu m} = <phi_mu | V S_m> (the
+   Q-matrix Eq.), and the Lehmann sums
+     G+_{mu nu}(z) = sum_m Q+_{mu m} Q+_{nu m} / (z + Omega~ - E+_m),
+     G-_{mu nu}(z) = sum_n Q-_{mu n} Q-_{nu n} / (z - Omega~ + E-_n),
+   G = G+ + G-, A(omega) = -Im sum_mu G_mu mu(omega + i eta) / pi.
+
+Orbitals mu = (site, spin).  All fp64.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import fock
+from . import hamiltonian as H
+
+
+def truncate(psi: np.ndarray, w_t: float):
+    """Indices of the kept coefficients (ascending) and the renormalised
+    coefficients on them (Sec. "Further truncation")."""
+    psi = np.asarray(psi, dtype=np.float64)
+    p = psi / np.linalg.norm(psi)
+    w = p * p
+    order = np.lexsort((np.arange(len(w)), -w))       # weight descending, index ascending
+    cum = np.cumsum(w[order])
+    k = int(np.searchsorted(cum, w_t * cum[-1] * (1 - 1e-15))) + 1
+    k = min(k, len(w))
+    keep = np.sort(order[:k])
+    c = p[keep]
+    return keep, c / np.linalg.norm(c)
+
+
+def excited_basis(words: np.ndarray, n: int, orbitals, dagger: bool) -> np.ndarray:
+    """Sorted unique words c^dag_mu w (dagger) or c_mu w over kept words w."""
+    out = set()
+    for w in map(int, words):
+        for site, spin in orbitals:
+            r = fock.create(w, n, spin, site) if dagger else fock.annihilate(w, n, 0, spin, site)
+            if r is not None:
+                out.add(r[0])
+    return np.array(sorted(out), dtype=np.uint64)
+
+
+def start_vectors(exc: np.ndarray, words: np.ndarray, coef: np.ndarray, n: int, orbitals,
+                  dagger: bool) -> np.ndarray:
+    """[len(exc), L]: column nu = c^dag_nu |Omega~> (or c_nu |Omega~>) in basis exc."""
+    Phi = np.zeros((len(exc), len(orbitals)))
+    pos = {int(w): i for i, w in enumerate(exc)}
+    for w, cw in zip(map(int, words), coef):
+        for nu, (site, spin) in enumerate(orbitals):
+            r = fock.create(w, n, spin, site) if dagger else fock.annihilate(w, n, 0, spin, site)
+            if r is not None:
+                Phi[pos[r[0]], nu] += r[1] * cw
+    return Phi
+
+
+def block_krylov(apply, Phi: np.ndarray, n_blocks: int, dtol: float = 1e-10):
+    """Orthonormal basis V of span{Phi, H Phi, ..., H^(n_blocks-1) Phi} and
+    H_eff = V^T H V.  Each candidate is orthogonalised against every earlier
+    basis vector (classical Gram-Schmidt, twice) and dropped ("deflated") when
+    its remaining norm is below dtol times its norm before."""
+    N = Phi.shape[0]
+    V = np.zeros((N, 0))
+
+    def extend(cands):
+        nonlocal V
+        added = []
+        for v in np.asarray(cands).T:
+            v = np.array(v, dtype=np.float64)
+            n0 = np.linalg.norm(v)
+            for _ in range(2):
+                B = np.column_stack([V] + added) if added else V
+                v = v - B @ (B.T @ v)
+            nv = np.linalg.norm(v)
+            if nv > dtol * max(n0, 1e-300):
+                added.append(v / nv)
+        blk = np.column_stack(added) if added else np.zeros((N, 0))
+        V = np.column_stack([V, blk])
+        return blk
+
+    blk = extend(Phi)
+    for _ in range(1, n_blocks):
+        if blk.shape[1] == 0:
+            break
+        blk = extend(np.column_stack([apply(blk[:, j]) for j in range(blk.shape[1])]))
+    HV = np.column_stack([apply(V[:, j]) for j in range(V.shape[1])]) if V.shape[1] else V
+    Heff = V.T @ HV
+    return V, 0.5 * (Heff + Heff.T)
+
+
+@dataclass
+class Poles:
+    E: np.ndarray       # eigenvalues of H_eff
+    Q: np.ndarray       # [L, K]
+    dim: int            # |F~+-|
+    krylov_dim: int
+
+
+def poles(model: H.Model, exc: np.ndarray, Phi: np.ndarray, n_blocks: int) -> Poles:
+    P = H.build(model, exc)
+    A = P.sparse()
+    V, Heff = block_krylov(lambda v: A @ v, Phi, n_blocks)
+    E, S = np.linalg.eigh(Heff)
+    Q = Phi.T @ (V @ S)                 # Q_{mu m} = <phi_mu | V S_m>
+    return Poles(E, Q, len(exc), V.shape[1])
+
+
+def exact_poles(model: H.Model, exc: np.ndarray, Phi: np.ndarray) -> Poles:
+    """All eigenpairs of H~ on the excited subspace (dense), Q = Phi^T S."""
+    P = H.build(model, exc)
+    E, S = np.linalg.eigh(P.dense())
+    return Poles(E, Phi.T @ S, len(exc), len(exc))
+
+
+def lehmann(p: Poles, E0: float, z: np.ndarray, particle: bool) -> np.ndarray:
+    """[nz, L, L]: sum_m Q_mu m Q_nu m / (z + E0 - E_m) (particle) or
+    / (z - E0 + E_m) (hole)."""
+    z = np.asarray(z, dtype=np.complex128)
+    den = (z[:, None] + E0 - p.E[None, :]) if particle else (z[:, None] - E0 + p.E[None, :])
+    return np.einsum("am,bm,zm->zab", p.Q, p.Q, 1.0 / den)
+
+
+@dataclass
+class GreenResult:
+    G: np.ndarray              # [nz, L, L] complex, G+ + G-
+    plus: Poles
+    minus: Poles
+    keep: np.ndarray
+    E0: float
+
+
+def green(model: H.Model, basis: np.ndarray, psi: np.ndarray, E0: float, orbitals, n_blocks: int,
+          w_t: float, z: np.ndarray, exact: bool = False) -> GreenResult:
+    """G_{mu nu}(z) of Eqs. (green), (green_qmatrix) in the truncated excited
+    subspaces.  Orbitals must share one spin (G is block diagonal in spin)."""
+    n = model.n
+    keep, coef = truncate(psi, w_t)
+    words = np.asarray(basis, dtype=np.uint64)[keep]
+    res = {}
+    for dag in (True, False):
+        exc = excited_basis(words, n, orbitals, dag)
+        Phi = start_vectors(exc, words, coef, n, orbitals, dag)
+        res[dag] = exact_poles(model, exc, Phi) if exact else poles(model, exc, Phi, n_blocks)
+    Gp = lehmann(res[True], E0, z, True)
+    Gm = lehmann(res[False], E0, z, False)
+    return GreenResult(Gp + Gm, res[True], res[False], keep, E0)
+
+
+def dos(G: np.ndarray) -> np.ndarray:
+    """A(omega) = -(1/pi) Im sum_mu G_mu mu (Eq. DOS)."""
+    return -np.imag(np.einsum("zaa->z", G)) / np.pi
