@@ -168,6 +168,36 @@ int mcd_connections_noalloc(mcd_ctx* ctx, int64_t* rows_dev, int64_t* cols_dev, 
 int mcd_lanczos_ground(mcd_ctx* ctx, int max_iter, double tol, uint64_t seed, int dtype,
                        double* E0, void* psi_dev, int* iters, double* residual);
 
+/* Sec. "Subspace of the Green function", Sec. "Further truncation", App. C:
+ * Green function of the ground state left by the last mcd_lanczos_ground
+ * (which keeps its normalised Ritz vector and E0).  The ground state is
+ * truncated to the shortest prefix of its largest |c_n|^2 (ties: lower index)
+ * reaching w_t of its norm and renormalised; F~+ = U_mu c^dag_mu F~ and
+ * F~- = U_mu c_mu F~; the start blocks c^dag_mu|Omega~>, c_mu|Omega~>; band
+ * Lanczos (blocked H~V, fp64 Gram-Schmidt twice against the last two blocks,
+ * rank-revealing Cholesky QR with deflation at 1e-10 (fp64) / 1e-5 (fp32) of a
+ * column's norm) for n_block_iter blocks in each space; the eigenpairs of the
+ * banded H_eff (fp64, host); Q = <phi_mu|E_m>; and
+ *   G_{mu nu}(z) = sum_m Q+_{mu m} Q+_{nu m} / (z + E0 - E+_m)
+ *                + sum_n Q-_{mu n} Q-_{nu n} / (z - E0 + E-_n).
+ * orb_site, orb_spin: host [L], 1 <= L <= 64, one spin for all (G is block
+ * diagonal in spin).  dtype: the Krylov vectors (MCD_F64 / MCD_F32).
+ * z_re, z_im: host [nz] (z = omega + i eta, or i omega_n).  G_re, G_im: host
+ * [nz][L][L].  dim_plus, dim_minus (nullable): |F~+|, |F~-|.  MCD_E_STATE
+ * without a ground state. */
+int mcd_band_lanczos_green(mcd_ctx* ctx, const int* orb_site, const int* orb_spin, int L,
+                           int n_block_iter, double w_t, int dtype, const double* z_re,
+                           const double* z_im, int nz, double* G_re, double* G_im,
+                           int64_t* dim_plus, int64_t* dim_minus);
+
+/* App. B/C (diagonalising the effective matrices): eigenvalues w[n]
+ * (ascending) of the symmetric host matrix A[n][n] (row-major; not modified)
+ * and the first `rows` rows of its eigenvector matrix X[rows][n] (column m =
+ * eigenvector of w[m]; X may be NULL).  Householder tridiagonalisation and
+ * implicit QR with the Wilkinson shift, fp64.  MCD_E_NOT_CONVERGED if the QR
+ * iteration cap is reached. */
+int mcd_symeig(int n, const double* A, double* w, int rows, double* X);
+
 /* Lanczos coefficients of the last mcd_lanczos_ground: a[cap], b[cap]
  * (b[0] = 0); *m = number of steps. Host arrays. */
 int mcd_lanczos_coeffs(const mcd_ctx* ctx, double* a, double* b, int cap, int* m);

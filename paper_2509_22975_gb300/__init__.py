@@ -53,6 +53,10 @@ _SIGS = {
                                           c_dp, c_vp, ctypes.POINTER(ctypes.c_int), c_dp]),
     "mcd_lanczos_coeffs": (ctypes.c_int, [c_vp, c_dp, c_dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "mcd_kernel_times": (ctypes.c_int, [c_vp, c_dp, c_i64p, ctypes.c_int, ctypes.c_int]),
+    "mcd_band_lanczos_green": (ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, c_dp, c_dp,
+                                              ctypes.c_int, c_dp, c_dp, c_i64p, c_i64p]),
+    "mcd_symeig": (ctypes.c_int, [ctypes.c_int, c_dp, c_dp, ctypes.c_int, c_dp]),
 }
 
 
@@ -81,6 +85,19 @@ def header_functions() -> list[str]:
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(mcd_[a-z0-9_]+)\s*\(", text)))
+
+
+def mcd_symeig(A, rows: int | None = None):
+    """Eigenvalues (ascending) and the first `rows` rows of the eigenvectors."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    rows = n if rows is None else rows
+    w = np.zeros(n)
+    X = np.zeros((rows, n))
+    st = lib().mcd_symeig(n, A.ctypes.data_as(c_dp), w.ctypes.data_as(c_dp), rows, X.ctypes.data_as(c_dp))
+    if st != MCD_OK:
+        raise MCDError(st, "mcd_symeig")
+    return w, X
 
 
 def _ptr(t) -> int:
@@ -229,6 +246,23 @@ class Context:
         self._check(self.L.mcd_lanczos_coeffs(self.h, a.ctypes.data_as(c_dp), b.ctypes.data_as(c_dp),
                                               m.value, ctypes.byref(m)))
         return a, b
+
+    def mcd_band_lanczos_green(self, orbitals, n_block_iter: int, w_t: float, z, dtype: int = MCD_F64):
+        """G[nz, L, L] (complex) of the last ground state; orbitals = [(site, spin)]."""
+        L = len(orbitals)
+        site = (ctypes.c_int * L)(*[int(o[0]) for o in orbitals])
+        spin = (ctypes.c_int * L)(*[int(o[1]) for o in orbitals])
+        z = np.ascontiguousarray(np.atleast_1d(z), dtype=np.complex128)
+        zr, zi = np.ascontiguousarray(z.real), np.ascontiguousarray(z.imag)
+        gr = np.zeros((len(z), L, L))
+        gi = np.zeros((len(z), L, L))
+        dp, dm = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._sync_stream()
+        self._check(self.L.mcd_band_lanczos_green(self.h, site, spin, L, n_block_iter, w_t, dtype,
+                                                  zr.ctypes.data_as(c_dp), zi.ctypes.data_as(c_dp), len(z),
+                                                  gr.ctypes.data_as(c_dp), gi.ctypes.data_as(c_dp),
+                                                  ctypes.byref(dp), ctypes.byref(dm)))
+        return gr + 1j * gi, dp.value, dm.value
 
     def mcd_kernel_times(self, reset: bool = False):
         ms = (ctypes.c_double * 4)()

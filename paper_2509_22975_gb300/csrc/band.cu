@@ -1,0 +1,593 @@
+// Band Lanczos Green function (Sec. "Subspace of the Green function",
+// Sec. "Further truncation", App. C) on the device.
+//
+// 1. Target-weight truncation of the ground state (host sort of |c_n|^2).
+// 2. Excited bases F~+ = U_mu c^dag_mu F~, F~- = U_mu c_mu F~ (host,
+//    sorted unique), each installed in an internal context of the
+//    neighbouring sector so that its H~ product runs on the same kernels.
+// 3. Start block Phi[:, nu] = c^(dag)_nu |Omega~> (kernel: for every excited
+//    state, remove/add the orbital's electron and search the kept ground-state
+//    words; the fermionic sign counts the occupied modes before the orbital).
+// 4. Band Lanczos in blocked form: W = H~ V_k (blocked H~V kernels, one
+//    column per active Krylov vector), A_k = V_k^T W, W -= V_k A_k +
+//    V_{k-1} B_k^T, repeated once (classical Gram-Schmidt twice, fp64 Gram
+//    matrices), then a rank-revealing Cholesky QR of W (column pivoting;
+//    columns whose remaining norm falls below 1e-10 of their norm before
+//    orthogonalisation are deflated, as band Lanczos does) gives V_{k+1} and
+//    B_{k+1}.  H_eff is block tridiagonal (banded) with blocks A_k, B_k.
+// 5. Eigenpairs of H_eff (host), Q = R0^T S[first block], and the Lehmann
+//    sums of the Q-matrix Eqs. summed over the particle and hole runs.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "mcd_internal.h"
+
+namespace mcd {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxOrb = 64;
+
+struct OrbParams {
+  int L;
+  int dagger;      // 1: start vectors c^dag |Omega>, 0: c |Omega>
+  int n_sites;
+  int site[kMaxOrb];
+  int spin[kMaxOrb];
+};
+
+// Phi[x][nu] = <x| c^(dag)_nu |Omega_t>, x in the excited basis.
+template <typename T>
+__global__ void start_vec_kernel(const uint64_t* __restrict__ exc, int64_t ne, const uint64_t* __restrict__ gw,
+                                 const double* __restrict__ gc, int64_t ng, T* phi, int ld, const OrbParams op) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= ne) return;
+  const uint64_t x = exc[k];
+  const int n = op.n_sites;
+  const uint64_t half = n == 32 ? 0xFFFFFFFFull : ((1ull << n) - 1);
+  for (int nu = 0; nu < op.L; ++nu) {
+    const int sh = op.spin[nu] == 0 ? n + op.site[nu] : op.site[nu];
+    const uint64_t bit = 1ull << sh;
+    double val = 0.0;
+    const bool present = (x & bit) != 0;
+    if (present == bool(op.dagger)) {
+      const uint64_t w = x ^ bit;   // the ground-state word the orbital acts on
+      int64_t lo = 0, len = ng;
+      while (len > 1) {
+        const int64_t h = len >> 1;
+        if (gw[lo + h] <= w) lo += h;
+        len -= h;
+      }
+      if (ng > 0 && gw[lo] == w) {
+        // occupied modes before the orbital's mode (order: up 0..n-1, dn 0..n-1)
+        const uint32_t up = uint32_t(w >> n), dn = uint32_t(w & half);
+        const int i = op.site[nu];
+        const uint32_t below = (i == 0) ? 0u : (0xFFFFFFFFu >> (32 - i));
+        const int before = op.spin[nu] == 0 ? __popc(up & below) : __popc(up) + __popc(dn & below);
+        val = (before & 1) ? -gc[lo] : gc[lo];
+      }
+    }
+    phi[k * ld + nu] = T(val);
+  }
+}
+
+// C[a][b] partial sums over rows of X[:, a] * Y[:, b]; one row of partials per CTA.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ X, int pa, const T* __restrict__ Y,
+                                                        int pb, int ld, int64_t n, double* partials) {
+  constexpr int kRows = 32;
+  __shared__ double xs[kRows][kMaxOrb];
+  __shared__ double ys[kRows][kMaxOrb];
+  const int npair = pa * pb;
+  constexpr int kPer = kMaxOrb * kMaxOrb / kThreads;   // 16 pairs per thread at most
+  double acc[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) acc[u] = 0.0;
+  for (int64_t r0 = int64_t(blockIdx.x) * kRows; r0 < n; r0 += int64_t(gridDim.x) * kRows) {
+    for (int e = threadIdx.x; e < kRows * kMaxOrb; e += kThreads) {
+      const int rr = e / kMaxOrb, cc = e % kMaxOrb;
+      const int64_t r = r0 + rr;
+      xs[rr][cc] = (r < n && cc < pa) ? double(X[r * ld + cc]) : 0.0;
+      ys[rr][cc] = (r < n && cc < pb) ? double(Y[r * ld + cc]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int pr = threadIdx.x + u * kThreads;
+      if (pr < npair) {
+        const int ia = pr / pb, ib = pr % pb;
+        double s = acc[u];
+        for (int rr = 0; rr < kRows; ++rr) s = fma(xs[rr][ia], ys[rr][ib], s);
+        acc[u] = s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int pr = threadIdx.x + u * kThreads;
+    if (pr < npair) partials[int64_t(blockIdx.x) * npair + pr] = acc[u];
+  }
+}
+
+__global__ void reduce_partials_kernel(const double* partials, int nparts, int npair, double* out) {
+  const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pr >= npair) return;
+  double s = 0.0;
+  for (int i = 0; i < nparts; ++i) s += partials[int64_t(i) * npair + pr];
+  out[pr] = s;
+}
+
+// W[r][j] = beta * W[r][j] + sum_i X1[r][i] C1[i][j] + sum_i X2[r][i] C2[i][j]
+// (C row-major [p_i][pw], fp64); out may alias W.
+template <typename T>
+__global__ void block_combine_kernel(const T* W, T* out, int pw, double beta, const T* X1, int p1,
+                                     const double* C1, const T* X2, int p2, const double* C2, int ld, int64_t n) {
+  const double* __restrict__ c1 = C1;
+  const double* __restrict__ c2 = C2;
+  const int64_t total = n * pw;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e / pw;
+    const int j = int(e - r * pw);
+    double s = beta == 0.0 ? 0.0 : beta * double(W[r * ld + j]);
+    for (int i = 0; i < p1; ++i) s = fma(double(X1[r * ld + i]), __ldg(c1 + i * pw + j), s);
+    for (int i = 0; i < p2; ++i) s = fma(double(X2[r * ld + i]), __ldg(c2 + i * pw + j), s);
+    out[r * ld + j] = T(s);
+  }
+}
+
+int grid_for(int64_t work) {
+  const int64_t g = (work + kThreads - 1) / kThreads;
+  return int(std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16)));
+}
+
+// Pivoted Cholesky of the p x p Gram G (row-major): G[piv, piv] = R^T R with
+// R upper triangular rank x p in pivoted column order.  Columns whose
+// remaining norm falls below dtol * ref[j] (norm before orthogonalisation)
+// are deflated.  Returns rank; piv[0..p) the column order.
+int pivoted_cholesky(int p, const std::vector<double>& G, const std::vector<double>& ref, double dtol,
+                     std::vector<int>& piv, std::vector<double>& R) {
+  std::vector<double> A = G;
+  piv.resize(p);
+  for (int i = 0; i < p; ++i) piv[i] = i;
+  R.assign(size_t(p) * p, 0.0);
+  int rank = 0;
+  for (int k = 0; k < p; ++k) {
+    // remaining diagonal of the Schur complement
+    // pivot: the column with the largest remaining norm relative to its norm
+    // before orthogonalisation; deflate the rest when that ratio is <= dtol
+    int best = -1;
+    double bestv = -1.0, bestrel = -1.0;
+    for (int j = k; j < p; ++j) {
+      const int c = piv[j];
+      double d = A[size_t(c) * p + c];
+      for (int i = 0; i < k; ++i) d -= R[size_t(i) * p + j] * R[size_t(i) * p + j];
+      const double rel = d / std::max(ref[c] * ref[c], 1e-300);
+      if (rel > bestrel) { bestrel = rel; bestv = d; best = j; }
+    }
+    if (best < 0 || bestv <= 0.0 || std::sqrt(std::max(bestrel, 0.0)) <= dtol) break;
+    // swap pivot into position k (also the R columns computed so far)
+    std::swap(piv[k], piv[best]);
+    for (int i = 0; i < k; ++i) std::swap(R[size_t(i) * p + k], R[size_t(i) * p + best]);
+    const double rkk = std::sqrt(bestv);
+    R[size_t(k) * p + k] = rkk;
+    for (int j = k + 1; j < p; ++j) {
+      double s = A[size_t(piv[k]) * p + piv[j]];
+      for (int i = 0; i < k; ++i) s -= R[size_t(i) * p + k] * R[size_t(i) * p + j];
+      R[size_t(k) * p + j] = s / rkk;
+    }
+    rank = k + 1;
+  }
+  return rank;
+}
+
+// M (p x r, row-major) with W * M = orthonormal block, from the pivoted
+// factor: M = P[:, :r] * inv(R11); and F (r x p) = R P^T so W ~ V F.
+void factors(int p, int r, const std::vector<int>& piv, const std::vector<double>& R, std::vector<double>& M,
+             std::vector<double>& F) {
+  // inverse of the r x r upper-triangular R11 (column order = pivot order)
+  std::vector<double> inv(size_t(r) * r, 0.0);
+  for (int j = 0; j < r; ++j) {
+    inv[size_t(j) * r + j] = 1.0 / R[size_t(j) * p + j];
+    for (int i = j - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1; k <= j; ++k) s += R[size_t(i) * p + k] * inv[size_t(k) * r + j];
+      inv[size_t(i) * r + j] = -s / R[size_t(i) * p + i];
+    }
+  }
+  M.assign(size_t(p) * r, 0.0);
+  for (int a = 0; a < r; ++a)
+    for (int j = 0; j < r; ++j) M[size_t(piv[a]) * r + j] = inv[size_t(a) * r + j];
+  F.assign(size_t(r) * p, 0.0);
+  for (int i = 0; i < r; ++i)
+    for (int b = 0; b < p; ++b) F[size_t(i) * p + piv[b]] = R[size_t(i) * p + b];
+}
+
+struct BandRun {
+  std::vector<double> E;   // eigenvalues of H_eff
+  std::vector<double> Q;   // [L][K]
+  int64_t dim = 0;
+  int K = 0;
+};
+
+template <typename T>
+class BandLanczos {
+ public:
+  BandLanczos(mcd_ctx* sub, int L) : c_(sub), L_(L), n_(sub->idx.n) {}
+  ~BandLanczos() {
+    for (void* p : {static_cast<void*>(B_[0]), static_cast<void*>(B_[1]), static_cast<void*>(B_[2]),
+                    static_cast<void*>(part_), static_cast<void*>(gram_), static_cast<void*>(coef_)})
+      if (p) cudaFree(p);
+  }
+
+  int alloc() {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&B_[i], size_t(n_) * L_ * sizeof(T) + 64);
+    nparts_ = grid_for(n_ / 32 + 1);
+    if (e == cudaSuccess) e = cudaMalloc(&part_, sizeof(double) * size_t(nparts_) * kMaxOrb * kMaxOrb);
+    if (e == cudaSuccess) e = cudaMalloc(&gram_, sizeof(double) * kMaxOrb * kMaxOrb);
+    if (e == cudaSuccess) e = cudaMalloc(&coef_, sizeof(double) * 2 * kMaxOrb * kMaxOrb);
+    if (e != cudaSuccess) return cuda_fail(c_, e, "band Lanczos buffers");
+    return MCD_OK;
+  }
+  T* buf(int i) { return B_[i]; }
+
+  // host G = X[:, :pa]^T Y[:, :pb]
+  int gram(const T* X, int pa, const T* Y, int pb, std::vector<double>& G) {
+    cudaStream_t s = c_->stream;
+    gram_kernel<T><<<nparts_, kThreads, 0, s>>>(X, pa, Y, pb, L_, n_, part_);
+    MCD_LAUNCHED(c_);
+    reduce_partials_kernel<<<(pa * pb + 255) / 256, 256, 0, s>>>(part_, nparts_, pa * pb, gram_);
+    MCD_LAUNCHED(c_);
+    G.resize(size_t(pa) * pb);
+    cudaError_t e = cudaMemcpyAsync(G.data(), gram_, sizeof(double) * pa * pb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? MCD_OK : cuda_fail(c_, e, "Gram");
+  }
+
+  // out = beta W + X1 C1 + X2 C2 (C1: p1 x pw, C2: p2 x pw)
+  int combine(const T* W, T* out, int pw, double beta, const T* X1, int p1, const std::vector<double>& C1,
+              const T* X2, int p2, const std::vector<double>& C2) {
+    cudaStream_t s = c_->stream;
+    std::vector<double> buf(2 * size_t(kMaxOrb) * kMaxOrb, 0.0);
+    std::copy(C1.begin(), C1.begin() + size_t(p1) * pw, buf.begin());
+    if (p2) std::copy(C2.begin(), C2.begin() + size_t(p2) * pw, buf.begin() + size_t(kMaxOrb) * kMaxOrb);
+    cudaError_t e = cudaMemcpyAsync(coef_, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
+    block_combine_kernel<T><<<grid_for(n_ * pw), kThreads, 0, s>>>(W, out, pw, beta, X1, p1, coef_, X2 ? X2 : X1,
+                                                                   p2, coef_ + size_t(kMaxOrb) * kMaxOrb, L_, n_);
+    MCD_LAUNCHED(c_);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // coef_ is reused by the next call
+    return e == cudaSuccess ? MCD_OK : cuda_fail(c_, e, "block combine");
+  }
+
+  // Orthonormalise the p columns of W (already orthogonal to the earlier
+  // blocks) into `out` with deflation: W ~ out * F, returns rank via r.
+  int qr(T* W, int p, const std::vector<double>& ref, T* out, int& r, std::vector<double>& F) {
+    std::vector<double> G, R, M, F1, G2, R2, M2, F2;
+    std::vector<int> piv;
+    int st = gram(W, p, W, p, G);
+    if (st) return st;
+    r = pivoted_cholesky(p, G, ref, sizeof(T) == 8 ? 1e-10 : 1e-5, piv, R);
+    if (r == 0) {
+      F.clear();
+      return MCD_OK;
+    }
+    factors(p, r, piv, R, M, F1);
+    st = combine(W, out, r, 0.0, W, p, M, nullptr, 0, M);
+    if (st) return st;
+    // second Cholesky QR pass (no deflation): out = out * R2^-1, F = R2 F1
+    st = gram(out, r, out, r, G2);
+    if (st) return st;
+    std::vector<double> one(r, 0.0);
+    std::vector<int> piv2;
+    const int r2 = pivoted_cholesky(r, G2, std::vector<double>(r, 1.0), 0.0, piv2, R2);
+    if (r2 != r) return fail(c_, MCD_E_BREAKDOWN, "band Lanczos: second QR pass lost rank");
+    factors(r, r, piv2, R2, M2, F2);
+    st = combine(out, W, r, 0.0, out, r, M2, nullptr, 0, M2);   // W temporarily holds the result
+    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(out, W, size_t(n_) * L_ * sizeof(T), cudaMemcpyDeviceToDevice, c_->stream);
+    if (e != cudaSuccess) return cuda_fail(c_, e, "copy block");
+    F.assign(size_t(r) * p, 0.0);
+    for (int i = 0; i < r; ++i)
+      for (int j = 0; j < p; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < r; ++k) s += F2[size_t(i) * r + k] * F1[size_t(k) * p + j];
+        F[size_t(i) * p + j] = s;
+      }
+    return MCD_OK;
+  }
+
+  // Runs the band Lanczos from the start block in buf(0) (L columns).
+  int run(int n_blocks, BandRun& out) {
+    T* Vprev = B_[1];
+    T* Vcur = B_[2];
+    T* W = B_[0];
+    std::vector<double> G0;
+    int st = gram(W, L_, W, L_, G0);
+    if (st) return st;
+    std::vector<double> ref(L_);
+    for (int j = 0; j < L_; ++j) ref[j] = std::sqrt(std::max(G0[size_t(j) * L_ + j], 0.0));
+    int p = 0;
+    std::vector<double> R0;
+    st = qr(W, L_, ref, Vcur, p, R0);
+    if (st) return st;
+    const int p1 = p;
+    std::vector<std::vector<double>> As, Bs;   // A_k (p_k x p_k), B_{k+1} (p_{k+1} x p_k)
+    std::vector<int> ps;
+    int pprev = 0;
+    std::vector<double> Bprev;   // B_k: p_k x p_{k-1}
+    for (int k = 0; k < n_blocks && p > 0; ++k) {
+      ps.push_back(p);
+      st = hv_apply(c_, Vcur, W, p, L_, sizeof(T) == 8 ? MCD_F64 : MCD_F32, nullptr, 0);
+      if (st) return st;
+      std::vector<double> Gw;
+      st = gram(W, p, W, p, Gw);
+      if (st) return st;
+      std::vector<double> refk(p);
+      for (int j = 0; j < p; ++j) refk[j] = std::sqrt(std::max(Gw[size_t(j) * p + j], 0.0));
+      // A = Vcur^T W ; W -= Vcur A + Vprev B_k^T
+      std::vector<double> A, C1, C2;
+      st = gram(Vcur, p, W, p, A);
+      if (st) return st;
+      std::vector<double> Bt;   // p_{k-1} x p_k
+      if (pprev) {
+        Bt.assign(size_t(pprev) * p, 0.0);
+        for (int i = 0; i < pprev; ++i)
+          for (int j = 0; j < p; ++j) Bt[size_t(i) * p + j] = -Bprev[size_t(j) * pprev + i];
+      }
+      std::vector<double> mA(A.size());
+      for (size_t i = 0; i < A.size(); ++i) mA[i] = -A[i];
+      st = combine(W, W, p, 1.0, Vcur, p, mA, pprev ? Vprev : nullptr, pprev, Bt);
+      if (st) return st;
+      // second Gram-Schmidt pass against the window
+      st = gram(Vcur, p, W, p, C1);
+      if (st) return st;
+      if (pprev) {
+        st = gram(Vprev, pprev, W, p, C2);
+        if (st) return st;
+      }
+      std::vector<double> mC1(C1.size()), mC2(C2.size());
+      for (size_t i = 0; i < C1.size(); ++i) mC1[i] = -C1[i];
+      for (size_t i = 0; i < C2.size(); ++i) mC2[i] = -C2[i];
+      st = combine(W, W, p, 1.0, Vcur, p, mC1, pprev ? Vprev : nullptr, pprev, mC2);
+      if (st) return st;
+      for (size_t i = 0; i < A.size(); ++i) A[i] += C1[i];
+      // symmetrise A
+      for (int i = 0; i < p; ++i)
+        for (int j = i + 1; j < p; ++j) {
+          const double v = 0.5 * (A[size_t(i) * p + j] + A[size_t(j) * p + i]);
+          A[size_t(i) * p + j] = A[size_t(j) * p + i] = v;
+        }
+      As.push_back(A);
+      if (k + 1 == n_blocks) break;
+      int r = 0;
+      std::vector<double> Bn;
+      st = qr(W, p, refk, Vprev, r, Bn);   // next block written over Vprev
+      if (st) return st;
+      if (r == 0) break;
+      Bs.push_back(Bn);
+      Bprev = Bn;
+      pprev = p;
+      p = r;
+      std::swap(Vprev, Vcur);   // Vcur <- new block, Vprev <- old current
+    }
+    // assemble the block tridiagonal H_eff
+    const int nb = int(As.size());
+    std::vector<int> off(nb + 1, 0);
+    for (int k = 0; k < nb; ++k) off[k + 1] = off[k] + ps[k];
+    const int K = off[nb];
+    std::vector<double> Hm(size_t(K) * K, 0.0);
+    for (int k = 0; k < nb; ++k) {
+      for (int i = 0; i < ps[k]; ++i)
+        for (int j = 0; j < ps[k]; ++j) Hm[size_t(off[k] + i) * K + off[k] + j] = As[k][size_t(i) * ps[k] + j];
+      if (k + 1 < nb) {
+        const std::vector<double>& Bk = Bs[k];   // p_{k+1} x p_k
+        for (int i = 0; i < ps[k + 1]; ++i)
+          for (int j = 0; j < ps[k]; ++j) {
+            Hm[size_t(off[k + 1] + i) * K + off[k] + j] = Bk[size_t(i) * ps[k] + j];
+            Hm[size_t(off[k] + j) * K + off[k + 1] + i] = Bk[size_t(i) * ps[k] + j];
+          }
+      }
+    }
+    out.E.assign(K, 0.0);
+    std::vector<double> X(size_t(p1) * K, 0.0);
+    if (symeig_leading(K, Hm.data(), out.E.data(), p1, X.data()) != 0)
+      return fail(c_, MCD_E_NOT_CONVERGED, "band Lanczos: H_eff eigensolver did not converge");
+    // Q[mu][m] = sum_{i < p1} R0[i][mu] X[i][m]
+    out.Q.assign(size_t(L_) * K, 0.0);
+    for (int mu = 0; mu < L_; ++mu)
+      for (int i = 0; i < p1; ++i) {
+        const double rv = R0[size_t(i) * L_ + mu];
+        if (rv == 0.0) continue;
+        for (int m = 0; m < K; ++m) out.Q[size_t(mu) * K + m] += rv * X[size_t(i) * K + m];
+      }
+    out.K = K;
+    out.dim = n_;
+    return MCD_OK;
+  }
+
+ private:
+  mcd_ctx* c_;
+  int L_;
+  int64_t n_;
+  T* B_[3] = {nullptr, nullptr, nullptr};
+  double* part_ = nullptr;
+  double* gram_ = nullptr;
+  double* coef_ = nullptr;
+  int nparts_ = 1;
+};
+
+template <typename T>
+int one_side(mcd_ctx* c, const std::vector<uint64_t>& kept_w, const std::vector<double>& kept_c, const int* site,
+             const int* spin, int L, bool dagger, int n_blocks, BandRun& out) {
+  const int n = c->n;
+  const int sp = spin[0];
+  // excited basis (host): c^dag_mu w or c_mu w over kept w
+  std::vector<uint64_t> exc;
+  exc.reserve(kept_w.size() * L);
+  for (uint64_t w : kept_w)
+    for (int mu = 0; mu < L; ++mu) {
+      const uint64_t bit = 1ull << (spin[mu] == 0 ? n + site[mu] : site[mu]);
+      const bool occ = (w & bit) != 0;
+      if (dagger && !occ) exc.push_back(w | bit);
+      if (!dagger && occ) exc.push_back(w ^ bit);
+    }
+  std::sort(exc.begin(), exc.end());
+  exc.erase(std::unique(exc.begin(), exc.end()), exc.end());
+  out.dim = int64_t(exc.size());
+  if (exc.empty()) {
+    out.K = 0;
+    return MCD_OK;
+  }
+  const int dnu = dagger ? 1 : -1;
+  const int nup = c->n_up + (sp == 0 ? dnu : 0), ndn = c->n_dn + (sp == 1 ? dnu : 0);
+  mcd_ctx* sub = nullptr;
+  int st = mcd_create(&sub, c->device, c->stream);
+  if (st) return fail(c, st, "band Lanczos: internal context");
+  struct Guard {
+    mcd_ctx* p;
+    ~Guard() { mcd_destroy(p); }
+  } guard{sub};
+  sub->hv_algo = c->hv_algo;
+  st = mcd_set_hamiltonian(sub, n, c->t.data(), c->eps.data(), c->U.data(), n, nup, ndn);
+  if (st == MCD_OK) st = mcd_set_basis(sub, exc.data(), int64_t(exc.size()));
+  if (st != MCD_OK) return fail(c, st, std::string("band Lanczos: excited space: ") + sub->err);
+  c->launches += sub->launches;
+  const int64_t before = sub->launches;
+  // kept ground-state words and coefficients on the device
+  uint64_t* dgw = nullptr;
+  double* dgc = nullptr;
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaMalloc(&dgw, kept_w.size() * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&dgc, kept_c.size() * 8);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dgw, kept_w.data(), kept_w.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dgc, kept_c.data(), kept_c.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    cudaFree(dgw);
+    cudaFree(dgc);
+    return cuda_fail(c, e, "ground-state words");
+  }
+  BandLanczos<T> bl(sub, L);
+  st = bl.alloc();
+  if (st == MCD_OK) {
+    OrbParams op;
+    std::memset(&op, 0, sizeof(op));
+    op.L = L;
+    op.dagger = dagger ? 1 : 0;
+    op.n_sites = n;
+    for (int mu = 0; mu < L; ++mu) {
+      op.site[mu] = site[mu];
+      op.spin[mu] = spin[mu];
+    }
+    const int64_t ne = int64_t(exc.size());
+    start_vec_kernel<T><<<int((ne + 255) / 256), 256, 0, s>>>(sub->idx.words, ne, dgw, dgc,
+                                                              int64_t(kept_w.size()), bl.buf(0), L, op);
+    MCD_LAUNCHED(sub);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(c, e, "start vectors");
+  }
+  if (st == MCD_OK) {
+    st = bl.run(n_blocks, out);
+    if (st != MCD_OK) c->err = sub->err;
+  }
+  c->launches += sub->launches - before;
+  cudaFree(dgw);
+  cudaFree(dgc);
+  return st;
+}
+
+}  // namespace
+
+int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int n_blocks, double w_t, int dtype,
+                       const double* z_re, const double* z_im, int nz, double* G_re, double* G_im,
+                       int64_t* dim_plus, int64_t* dim_minus) {
+  if (!c->gs_valid) return fail(c, MCD_E_STATE, "no ground state: call mcd_lanczos_ground first");
+  if (L < 1 || L > kMaxOrb) return fail(c, MCD_E_INVALID, "need 1 <= L <= 64 orbitals");
+  for (int mu = 0; mu < L; ++mu) {
+    if (site[mu] < 0 || site[mu] >= c->n || (spin[mu] != 0 && spin[mu] != 1))
+      return fail(c, MCD_E_INVALID, "orbital (site, spin) out of range");
+    if (spin[mu] != spin[0])
+      return fail(c, MCD_E_INVALID, "orbitals must share one spin (G is block diagonal in spin)");
+  }
+  if (n_blocks < 1) return fail(c, MCD_E_INVALID, "n_block_iter must be >= 1");
+  if (!(w_t > 0.0 && w_t <= 1.0)) return fail(c, MCD_E_INVALID, "w_t must be in (0, 1]");
+  const int64_t N = c->idx.n;
+  // target-weight truncation (Sec. "Further truncation"): largest |c|^2 first,
+  // ties by basis index, shortest prefix reaching w_t of the norm
+  std::vector<double> psi(N);
+  cudaError_t e = cudaMemcpyAsync(psi.data(), c->gs_psi, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy ground state");
+  double nn = 0.0;
+  for (double v : psi) nn += v * v;
+  const double inv = 1.0 / std::sqrt(nn);
+  std::vector<double> wgt(N);
+  for (int64_t i = 0; i < N; ++i) {
+    const double p = psi[i] * inv;
+    wgt[i] = p * p;
+  }
+  std::vector<int64_t> order(N);
+  for (int64_t i = 0; i < N; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return wgt[a] > wgt[b]; });
+  std::vector<double> cum(N);
+  double run = 0.0;
+  for (int64_t i = 0; i < N; ++i) cum[i] = (run += wgt[order[i]]);
+  const double target = w_t * cum[N - 1] * (1.0 - 1e-15);
+  int64_t k = int64_t(std::lower_bound(cum.begin(), cum.end(), target) - cum.begin()) + 1;
+  if (k > N) k = N;
+  std::vector<int64_t> keep(order.begin(), order.begin() + k);
+  std::sort(keep.begin(), keep.end());
+  std::vector<uint64_t> kw(k);
+  std::vector<double> kc(k);
+  double kn = 0.0;
+  for (int64_t i = 0; i < k; ++i) {
+    kw[i] = c->basis_on_host ? c->basis[keep[i]] : 0;
+    kc[i] = psi[keep[i]];
+    kn += kc[i] * kc[i];
+  }
+  if (!c->basis_on_host) {
+    std::vector<uint64_t> all(N);
+    e = cudaMemcpy(all.data(), c->idx.words, sizeof(uint64_t) * N, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy basis");
+    for (int64_t i = 0; i < k; ++i) kw[i] = all[keep[i]];
+  }
+  for (double& v : kc) v /= std::sqrt(kn);
+  BandRun plus, minus;
+  int st = dtype == MCD_F64 ? one_side<double>(c, kw, kc, site, spin, L, true, n_blocks, plus)
+                            : one_side<float>(c, kw, kc, site, spin, L, true, n_blocks, plus);
+  if (st == MCD_OK)
+    st = dtype == MCD_F64 ? one_side<double>(c, kw, kc, site, spin, L, false, n_blocks, minus)
+                          : one_side<float>(c, kw, kc, site, spin, L, false, n_blocks, minus);
+  if (st != MCD_OK) return st;
+  if (dim_plus) *dim_plus = plus.dim;
+  if (dim_minus) *dim_minus = minus.dim;
+  // Lehmann sums: G+ = sum Q Q / (z + E0 - E+), G- = sum Q Q / (z - E0 + E-)
+  const double E0 = c->gs_E0;
+  for (int iz = 0; iz < nz; ++iz) {
+    for (int a = 0; a < L; ++a)
+      for (int b = 0; b < L; ++b) {
+        double re = 0.0, im = 0.0;
+        for (int side = 0; side < 2; ++side) {
+          const BandRun& R = side == 0 ? plus : minus;
+          for (int m = 0; m < R.K; ++m) {
+            const double q = R.Q[size_t(a) * R.K + m] * R.Q[size_t(b) * R.K + m];
+            if (q == 0.0) continue;
+            const double dr = side == 0 ? z_re[iz] + E0 - R.E[m] : z_re[iz] - E0 + R.E[m];
+            const double di = z_im[iz];
+            const double d2 = dr * dr + di * di;
+            re += q * dr / d2;
+            im -= q * di / d2;
+          }
+        }
+        G_re[(size_t(iz) * L + a) * L + b] = re;
+        G_im[(size_t(iz) * L + a) * L + b] = im;
+      }
+  }
+  return MCD_OK;
+}
+
+}  // namespace mcd

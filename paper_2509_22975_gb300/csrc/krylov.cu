@@ -423,6 +423,18 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "Ritz residual");
   *resid_out = std::sqrt(rr / nn);
+  // keep the normalised ground state for the Green function
+  if (!c->gs_psi || c->gs_n != n) {
+    if (c->gs_psi) cudaFree(c->gs_psi);
+    c->gs_psi = nullptr;
+    e = cudaMalloc(&c->gs_psi, sizeof(double) * n);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ground-state copy");
+    c->gs_n = n;
+  }
+  cast_scale_kernel<double><<<vg, kThreads, 0, s>>>(c->gs_psi, p64, n, 1.0 / std::sqrt(nn));
+  MCD_LAUNCHED(c);
+  c->gs_E0 = E0;
+  c->gs_valid = true;
   if (psi) {
     cast_scale_kernel<T><<<vg, kThreads, 0, s>>>(psi, p64, n, 1.0 / std::sqrt(nn));
     MCD_LAUNCHED(c);

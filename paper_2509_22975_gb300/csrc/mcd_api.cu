@@ -43,6 +43,7 @@ int need_basis(mcd_ctx* c) {
 }
 
 int install_basis(mcd_ctx* c, std::vector<uint64_t>&& words) {
+  c->gs_valid = false;
   c->basis = std::move(words);
   c->n_basis = int64_t(c->basis.size());
   c->basis_on_host = true;
@@ -116,6 +117,7 @@ int mcd_destroy(mcd_ctx* c) {
     if (c->d_eps) cudaFree(c->d_eps);
     if (c->d_U) cudaFree(c->d_U);
     if (c->d_pclass) cudaFree(c->d_pclass);
+    if (c->gs_psi) cudaFree(c->gs_psi);
     if (c->tm) {
       if (c->tm->created)
         for (auto& ev : c->tm->ev) cudaEventDestroy(ev);
@@ -421,6 +423,7 @@ int mcd_set_basis_device(mcd_ctx* c, const uint64_t* w, int64_t n) {
   c->basis.clear();
   c->basis_on_host = false;
   c->n_basis = 0;
+  c->gs_valid = false;
   st = build_index(c, w, n, true);
   if (st != MCD_OK) return st;
   c->n_basis = n;
@@ -521,6 +524,31 @@ int mcd_lanczos_ground(mcd_ctx* c, int max_iter, double tol, uint64_t seed, int 
   if (dtype != MCD_F64 && dtype != MCD_F32) return fail(c, MCD_E_INVALID, "dtype must be MCD_F64 or MCD_F32");
   if (!std::isfinite(tol)) return fail(c, MCD_E_INVALID, "tol must be finite");
   return lanczos_ground(c, max_iter, tol, seed, dtype, E0, psi, iters, residual);
+}
+
+int mcd_band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int n_block_iter, double w_t,
+                           int dtype, const double* z_re, const double* z_im, int nz, double* G_re, double* G_im,
+                           int64_t* dim_plus, int64_t* dim_minus) {
+  if (!c) return MCD_E_INVALID;
+  int st = need_basis(c);
+  if (st != MCD_OK) return st;
+  if ((st = need_device(c)) != MCD_OK) return st;
+  if (!site || !spin || nz < 0 || (nz > 0 && (!z_re || !z_im || !G_re || !G_im)))
+    return fail(c, MCD_E_INVALID, "null argument");
+  if (dtype != MCD_F64 && dtype != MCD_F32) return fail(c, MCD_E_INVALID, "dtype must be MCD_F64 or MCD_F32");
+  try {
+    return band_lanczos_green(c, site, spin, L, n_block_iter, w_t, dtype, z_re, z_im, nz, G_re, G_im, dim_plus,
+                              dim_minus);
+  } catch (const std::bad_alloc&) {
+    return fail(c, MCD_E_OOM, "band Lanczos: out of host memory");
+  }
+}
+
+int mcd_symeig(int n, const double* A, double* w, int rows, double* X) {
+  if (n < 0 || (n > 0 && (!A || !w)) || rows < 0) return MCD_E_INVALID;
+  if (n == 0) return MCD_OK;
+  std::vector<double> work(A, A + size_t(n) * n);
+  return symeig_leading(n, work.data(), w, X ? rows : 0, X) == 0 ? MCD_OK : MCD_E_NOT_CONVERGED;
 }
 
 int mcd_lanczos_coeffs(const mcd_ctx* c, double* a, double* b, int cap, int* m) {

@@ -135,6 +135,10 @@ struct mcd_ctx {
   mcd::DevIndex idx;
   // Krylov
   mcd::LanczosWork lw;
+  double* gs_psi = nullptr;            // normalised ground state (fp64, device)
+  int64_t gs_n = 0;
+  double gs_E0 = 0.0;
+  bool gs_valid = false;
   std::vector<double> last_a, last_b;
   // Options
   int hv_algo = 0;
@@ -155,8 +159,16 @@ int sample_basis(mcd_ctx* c, uint64_t seed, int64_t n_target, double beta,
                  std::vector<uint64_t>& out);
 double sector_size(int n, int n_up, int n_dn);
 
-// host eigensolvers (tridiag.cpp)
+// host eigensolvers (tridiag.cpp, symeig.cpp)
 double tridiag_lowest(const double* a, const double* b, int m, double* vec /*nullable [m]*/);
+// eigenvalues w[n] ascending of symmetric A (row-major n x n, destroyed) and the
+// leading `rows` rows of the eigenvector matrix X[rows][n]; 0 on success
+int symeig_leading(int n, double* A, double* w, int rows, double* X);
+
+// band Lanczos Green function (band.cu)
+int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int n_blocks, double w_t, int dtype,
+                       const double* z_re, const double* z_im, int nz, double* G_re, double* G_im,
+                       int64_t* dim_plus, int64_t* dim_minus);
 
 // device index (index.cu)
 int build_index(mcd_ctx* c, const uint64_t* words, int64_t n, bool on_device);
