@@ -17,6 +17,7 @@
 // targets are broadcast within the group by shuffles, then every lane
 // gathers its column chunk of the target row (coalesced 16-byte loads when
 // the rows are aligned).
+#include <algorithm>
 #include <cmath>
 
 #include "mcd_internal.h"
@@ -28,6 +29,7 @@ constexpr int kThreads = 256;
 constexpr int kBitmapMaxSites = 16;            // 2^16-bit bitmap = 8 KiB of shared memory
 constexpr int kStageXBytes = 52 * 1024;        // x staging area of the bitmap kernel
 constexpr int kStageX1Bytes = 20 * 1024;       // x staging area of the single-column kernel
+constexpr int kStageXcBytes = 72 * 1024;       // shared memory of the multi-column kernel
 
 struct HvArgs {
   const void* x;
@@ -45,6 +47,7 @@ struct HvArgs {
   int off_bm, off_pre, off_xs;
   int xs_cap;             // elements of T that fit in the x staging area
   int off_pt;             // single-column kernel: partner table
+  int off_list, off_cnt;  // multi-column kernel: per-state connection lists
   int ncp;                // staged row stride: ncols rounded up to VEC
 };
 
@@ -810,6 +813,208 @@ __global__ void __launch_bounds__(kThreads) hv_l1_kernel(const HvArgs a, const H
 }
 
 // ---------------------------------------------------------------------------------
+// Multi-column variant (H~V, band Lanczos).  Rounds of 256 states; in phase
+// 1 one thread per state enumerates its active hops from the partner classes
+// and looks them up once, writing each found target as a 2-byte record
+// (block-local index | sign << 14 | class-half << 15) into a shared list per
+// class pair (at most 32 records: one per bit of the pair's mask).  In phase
+// 2 groups of G lanes read the lists of their states and gather and sum the
+// VEC columns each lane owns (from staged block rows when they fit).
+template <typename T, int VEC, int G, bool PASS_A>
+__global__ void __launch_bounds__(kThreads) hv_lc_kernel(const HvArgs a, const HamParams hp) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __shared__ uint32_t s_b0, s_b1;
+  __shared__ float s_dhi[kMaxSites + 1], s_dlo[kMaxSites + 1];
+  __shared__ double s_d64[kMaxSites + 1];
+  uint2* s_pt = reinterpret_cast<uint2*>(s_dyn + a.off_pt);
+  uint2* bm = reinterpret_cast<uint2*>(s_dyn + a.off_bm);
+  T* xs = reinterpret_cast<T*>(s_dyn + a.off_xs);
+  uint16_t* lists = reinterpret_cast<uint16_t*>(s_dyn + a.off_list);   // [256][npairs][32]
+  uint8_t* cnts = reinterpret_cast<uint8_t*>(s_dyn + a.off_cnt);        // [256][npairs]
+  const Layout& L = a.L;
+  const int item = blockIdx.x;
+  const int64_t k0 = int64_t(item) * kItem;
+  const int64_t k1 = (k0 + kItem < L.n) ? k0 + kItem : L.n;
+  const int ng = (hp.n_pcls + 3) / 4;
+  const int npairs = (hp.n_pcls + 1) / 2;
+  for (int i = threadIdx.x; i < a.nw; i += kThreads) bm[i] = make_uint2(0u, 0u);
+  for (int i = threadIdx.x; i < ng * 512 + hp.n_pcls * 16; i += kThreads) s_pt[i] = hp.ptab[i];
+  if (threadIdx.x <= kMaxSites) {
+    s_dhi[threadIdx.x] = hp.dtab_hi[threadIdx.x];
+    s_dlo[threadIdx.x] = hp.dtab_lo[threadIdx.x];
+    s_d64[threadIdx.x] = hp.dtab[threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    const uint32_t b0 = L.item_blk[item];
+    uint32_t b1 = L.item_blk[item + 1];
+    if (b1 == uint32_t(L.nblk) || L.blk_off[b1] == uint32_t(k1)) b1 -= 1;
+    s_b0 = b0;
+    s_b1 = b1;
+  }
+  __syncthreads();
+  const uint2* ptab = s_pt;
+  const uint2* pflip = s_pt + ng * 512;
+  const T* __restrict__ x = static_cast<const T*>(a.x);
+  T* __restrict__ y = static_cast<T*>(a.y);
+  const int g = threadIdx.x % G;
+  const int group = threadIdx.x / G;
+  constexpr int kGroups = kThreads / G;
+  const int ncols = a.ncols, ld = a.ld, ncp = a.ncp;
+  const int col = g * VEC;
+  const int cvalid = ncols - col;
+  using C = ChunkOf<T, VEC>;
+  uint16_t* mylist = lists + threadIdx.x * npairs * 32;
+  uint8_t* mycnt = cnts + threadIdx.x * npairs;
+
+  for (uint32_t blk = s_b0; blk <= s_b1; ++blk) {
+    const int bs = int(L.blk_off[blk]), be = int(L.blk_off[blk + 1]);
+    const uint32_t major = L.blk_major[blk];
+    const int bsz = be - bs;
+    const bool staged = int64_t(bsz) * ncp <= a.xs_cap;
+    for (int q = threadIdx.x; q < bsz; q += kThreads) {
+      const uint32_t d = L.minor[bs + q];
+      atomicOr(&bm[d >> 5].x, 1u << (d & 31));
+      if (q == 0 || (L.minor[bs + q - 1] >> 5) != (d >> 5)) bm[d >> 5].y = uint32_t(q);
+    }
+    if (staged && col < ncp) {
+      for (int q = group; q < bsz; q += kGroups) {
+        const int64_t row = PASS_A ? int64_t(bs + q) : int64_t(L.perm[bs + q]);
+        T v[VEC];
+        C::load(x + row * ld + col, cvalid, v);
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) xs[q * ncp + col + u] = v[u];
+      }
+    }
+    __syncthreads();
+    const int lo = (int64_t(bs) > k0) ? bs : int(k0);
+    const int hi = (int64_t(be) < k1) ? be : int(k1);
+    for (int r0 = lo; r0 < hi; r0 += kThreads) {
+      // phase 1: lookups, one thread per state
+      {
+        const int k = r0 + threadIdx.x;
+        if (k < hi) {
+          const uint32_t m = L.minor[k];
+          const uint32_t mm = m | (m << 16);
+          for (int gi = 0; gi < ng; ++gi) {
+            const uint2 t0 = ptab[gi * 512 + (m & 255u)];
+            const uint2 t1 = ptab[gi * 512 + 256 + (m >> 8)];
+            for (int h = 0; h < 2; ++h) {
+              const int c = 4 * gi + 2 * h;
+              if (c >= hp.n_pcls) break;
+              const bool pair = c + 1 < hp.n_pcls;
+              const uint32_t pp = h ? (t0.y | t1.y) : (t0.x | t1.x);
+              uint32_t act = (mm ^ pp) & (hp.pfirst[c] | (pair ? hp.pfirst[c + 1] << 16 : 0u));
+              const uint2* fl = pflip + c * 16;
+              uint16_t* out = mylist + (c >> 1) * 32;
+              int nf = 0;
+              while (act) {
+                const int i1 = __ffs(act) - 1;
+                act &= act - 1u;
+                const uint2 f1 = fl[i1];
+                const int q1 = l1_find(bm, m ^ f1.x);
+                if (q1 >= 0)
+                  out[nf++] = uint16_t(q1 | ((__popc(m & f1.y) & 1u) << 14) | ((i1 >> 4) << 15));
+              }
+              mycnt[c >> 1] = uint8_t(nf);
+            }
+          }
+        } else {
+          for (int pi = 0; pi < npairs; ++pi) mycnt[pi] = 0;
+        }
+      }
+      __syncthreads();
+      // phase 2: gathers, G lanes per state
+      const int ns = (hi - r0 < kThreads) ? hi - r0 : kThreads;
+      for (int t = group; t < ns; t += kGroups) {
+        const int k = r0 + t;
+        const uint16_t* lt = lists + t * npairs * 32;
+        const uint8_t* ct = cnts + t * npairs;
+        Acc<T> acc[VEC];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) acc[u].zero();
+        for (int pi = 0; pi < npairs; ++pi) {
+          const int c = 2 * pi;
+          const bool pair = c + 1 < hp.n_pcls;
+          T s0[VEC], s1[VEC];
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) s0[u] = s1[u] = T(0);
+          const int nf = ct[pi];
+          for (int j = 0; j < nf; ++j) {
+            const uint32_t e = lt[pi * 32 + j];
+            const int q = int(e & 0x3FFFu);
+            if (cvalid <= 0) continue;
+            T xv[VEC];
+            if (staged) {
+#pragma unroll
+              for (int u = 0; u < VEC; ++u) xv[u] = xs[q * ncp + col + u];
+            } else {
+              const int64_t row = PASS_A ? int64_t(bs + q) : int64_t(L.perm[bs + q]);
+              C::load(x + row * ld + col, cvalid, xv);
+            }
+            if (e & 0x4000u) {
+#pragma unroll
+              for (int u = 0; u < VEC; ++u) xv[u] = -xv[u];
+            }
+            if (e & 0x8000u) {
+#pragma unroll
+              for (int u = 0; u < VEC; ++u) s1[u] += xv[u];
+            } else {
+#pragma unroll
+              for (int u = 0; u < VEC; ++u) s0[u] += xv[u];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) {
+            if (sizeof(T) == 4) {
+              acc[u].fma(T(hp.pcls_hi[c]), T(hp.pcls_lo[c]), s0[u]);
+              if (pair) acc[u].fma(T(hp.pcls_hi[c + 1]), T(hp.pcls_lo[c + 1]), s1[u]);
+            } else {
+              acc[u].fma(T(hp.pcls_t[c]), T(0), s0[u]);
+              if (pair) acc[u].fma(T(hp.pcls_t[c + 1]), T(0), s1[u]);
+            }
+          }
+        }
+        if (cvalid > 0) {
+          T out[VEC];
+          if (PASS_A) {
+            const uint32_t m = L.minor[k];
+            T xv[VEC], yv[VEC];
+            if (staged) {
+#pragma unroll
+              for (int u = 0; u < VEC; ++u) xv[u] = xs[(k - bs) * ncp + col + u];
+            } else {
+              C::load(x + int64_t(k) * ld + col, cvalid, xv);
+            }
+            C::load(y + int64_t(k) * ld + col, cvalid, yv);
+            const int nu = __popc(major & m);
+            Coef<T> dc;
+            if (hp.uniform) {
+              dc.hi = sizeof(T) == 4 ? T(s_dhi[nu]) : T(s_d64[nu]);
+              dc.lo = sizeof(T) == 4 ? T(s_dlo[nu]) : T(0);
+            } else {
+              dc = diag_coef<T>(hp, major, m);
+            }
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) {
+              acc[u].fma(dc.hi, dc.lo, xv[u]);
+              out[u] = acc[u].value() + yv[u];
+            }
+            C::store(y + int64_t(k) * ld + col, cvalid, out);
+          } else {
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) out[u] = acc[u].value();
+            C::store(y + int64_t(L.perm[k]) * ld + col, cvalid, out);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    for (int q = threadIdx.x; q < bsz; q += kThreads) bm[L.minor[bs + q] >> 5].x = 0u;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // Plain path: one thread per state, both spins, binary search over the whole
 // sorted basis in global memory.  Kept as the simple reference GPU path.
 template <typename T>
@@ -990,6 +1195,40 @@ cudaError_t launch_pair(mcd_ctx* c, const void* x, void* y, int ncols, int ld, d
       hv_l1_kernel<T, true, true><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
     else
       hv_l1_kernel<T, true, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+    MCD_LAUNCHED(c);
+    timing_end(c);
+    return cudaGetLastError();
+  }
+  const bool lc = bitmap && !l1 && c->hp->n_pcls > 0 && c->hp->n_pcls <= 8 && !partials && ncols <= G * VEC;
+  if (lc) {
+    // layout: [ptab + flips][bm: nw uint2][lists: 256 x npairs x 32 u16][counts: 256 x npairs][xs]
+    const int ngp = (c->hp->n_pcls + 3) / 4;
+    const int npairs = (c->hp->n_pcls + 1) / 2;
+    a.off_pt = 0;
+    a.off_bm = (ngp * 512 + c->hp->n_pcls * 16) * 8;
+    a.off_list = a.off_bm + 8 * a.nw;
+    a.off_cnt = a.off_list + kThreads * npairs * 32 * 2;
+    a.off_xs = (a.off_cnt + kThreads * npairs + 15) & ~15;
+    // staging area: what is left of ~72 KiB (three CTAs per SM), at least 4 KiB
+    const int xs_bytes = std::max(4096, kStageXcBytes - a.off_xs) & ~15;
+    smem = size_t(a.off_xs) + xs_bytes;
+    a.xs_cap = int(xs_bytes / sizeof(T));
+    static int configured_lc = -1;
+    if (configured_lc < int(smem)) {
+      cudaFuncSetAttribute(hv_lc_kernel<T, VEC, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      cudaFuncSetAttribute(hv_lc_kernel<T, VEC, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      configured_lc = int(smem);
+    }
+    a.L = c->idx.B;
+    timing_begin(c, 0);
+    hv_lc_kernel<T, VEC, G, false><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
+    MCD_LAUNCHED(c);
+    timing_end(c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    a.L = c->idx.A;
+    timing_begin(c, 1);
+    hv_lc_kernel<T, VEC, G, true><<<int(a.L.n_items), kThreads, smem, c->stream>>>(a, *c->hp);
     MCD_LAUNCHED(c);
     timing_end(c);
     return cudaGetLastError();
