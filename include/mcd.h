@@ -126,6 +126,18 @@ int mcd_basis_info(mcd_ctx* ctx, int64_t* n_states, int64_t* n_up_blocks,
  * two floats) and accumulate each row in fp32. */
 int mcd_apply(mcd_ctx* ctx, const void* x, void* y, int ncols, int ld, int dtype);
 
+/* Adjoint of mcd_apply with respect to the parameters of Eq. (1): for device
+ * blocks u, v (dtype, [n_states][ld], ncols columns), the derivatives of
+ * <u, H~ v> = sum_c u[:, c]^T H~ v[:, c], accumulated in fp64:
+ *   grad_t[i*n+j] = grad_t[j*n+i] = d/dt_ij for every bond with t_ij != 0
+ *                   (one parameter per bond; 0 elsewhere),
+ *   grad_eps[i]   = d/deps_i,   grad_U[i] = d/dU_i.
+ * Host outputs, each nullable.  With u = v = |Omega~> these are the
+ * Hellmann-Feynman derivatives of E0; the adjoint with respect to v is H~ u
+ * (mcd_apply), H~ being symmetric. */
+int mcd_hv_adjoint(mcd_ctx* ctx, const void* u, const void* v, int ncols, int ld, int dtype,
+                   double* grad_t, double* grad_eps, double* grad_U);
+
 /* Diagonal <x~_k|H|x~_k> of H~ in fp64, written to device diag_dev[n_states]. */
 int mcd_diagonal(mcd_ctx* ctx, double* diag_dev);
 

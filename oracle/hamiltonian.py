@@ -154,3 +154,34 @@ def apply_rows(model: Model, basis: np.ndarray, x: np.ndarray, ks) -> tuple[np.n
             Y[a, col] = math.fsum(terms)
             S[a, col] = math.fsum(abs(t) for t in terms)
     return Y, S
+
+
+def parameter_derivatives(model: Model, basis, u: np.ndarray, v: np.ndarray):
+    """d<u, H~ v>/d(t_ij, eps_i, U_i) from the plain definition: H~ is linear
+    in its parameters, so each derivative is <u, D v> with D the projected
+    Hamiltonian of that parameter alone set to 1 (for t_ij: the bond (i, j)
+    with t_ij = t_ji = 1).  Returns (grad_t [n, n] symmetric, 0 off the bonds,
+    grad_eps [n], grad_U [n]); u, v are [N] or [N, L] (summed over columns)."""
+    n = model.n
+    U_ = np.asarray(u, dtype=np.float64).reshape(len(basis), -1)
+    V_ = np.asarray(v, dtype=np.float64).reshape(len(basis), -1)
+    zero = np.zeros(n)
+    gt = np.zeros((n, n))
+    for i in range(n):
+        for j in range(i + 1, n):
+            if model.t[i, j] == 0.0:
+                continue
+            T = np.zeros((n, n))
+            T[i, j] = T[j, i] = 1.0
+            D = build(Model(n, T, zero, zero), basis).sparse()
+            gt[i, j] = gt[j, i] = float(np.sum(U_ * (D @ V_)))
+    ge = np.zeros(n)
+    gu = np.zeros(n)
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        de = fock.diagonal(np.asarray(basis, dtype=np.uint64), n, e, zero)
+        du = fock.diagonal(np.asarray(basis, dtype=np.uint64), n, zero, e)
+        ge[i] = float(np.sum(U_ * (de[:, None] * V_)))
+        gu[i] = float(np.sum(U_ * (du[:, None] * V_)))
+    return gt, ge, gu

@@ -57,6 +57,7 @@ _SIGS = {
                                               ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, c_dp, c_dp,
                                               ctypes.c_int, c_dp, c_dp, c_i64p, c_i64p]),
     "mcd_symeig": (ctypes.c_int, [ctypes.c_int, c_dp, c_dp, ctypes.c_int, c_dp]),
+    "mcd_hv_adjoint": (ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_dp, c_dp, c_dp]),
 }
 
 
@@ -156,8 +157,10 @@ class Context:
         e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
         u = np.ascontiguousarray(np.atleast_1d(U), dtype=np.float64)
         ep = e.ctypes.data_as(c_dp) if e is not None else None
-        return self._check(self.L.mcd_set_hamiltonian(self.h, n, t.ctypes.data_as(c_dp), ep,
-                                                      u.ctypes.data_as(c_dp), len(u), n_up, n_dn))
+        st = self._check(self.L.mcd_set_hamiltonian(self.h, n, t.ctypes.data_as(c_dp), ep,
+                                                    u.ctypes.data_as(c_dp), len(u), n_up, n_dn))
+        self.n_sites, self.n_up, self.n_dn = n, n_up, n_dn
+        return st
 
     def mcd_build_basis(self, seed: int, n_target: int, beta: float, seed_states, flags: int = 0):
         s = np.ascontiguousarray(np.atleast_1d(seed_states), dtype=np.uint64)
@@ -206,6 +209,17 @@ class Context:
         l = l if ld is None else ld
         self._sync_stream()
         return self._check(self.L.mcd_apply(self.h, _ptr(x), _ptr(y), nc, l, _dtype_code(x)))
+
+    def mcd_hv_adjoint(self, u, v):
+        """(grad_t [n, n], grad_eps [n], grad_U [n]) of <u, H~ v> (torch device tensors)."""
+        n = self.n_sites
+        gt, ge, gu = np.zeros((n, n)), np.zeros(n), np.zeros(n)
+        nc, l = (1, 1) if u.dim() == 1 else (u.shape[1], u.stride(0))
+        self._sync_stream()
+        self._check(self.L.mcd_hv_adjoint(self.h, _ptr(u), _ptr(v), nc, l, _dtype_code(u),
+                                          gt.ctypes.data_as(c_dp), ge.ctypes.data_as(c_dp),
+                                          gu.ctypes.data_as(c_dp)))
+        return gt, ge, gu
 
     def mcd_diagonal(self, out):
         self._sync_stream()

@@ -495,6 +495,18 @@ int mcd_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype) 
   return hv_apply(c, x, y, ncols, ld, dtype, nullptr, 0);
 }
 
+int mcd_hv_adjoint(mcd_ctx* c, const void* u, const void* v, int ncols, int ld, int dtype, double* grad_t,
+                   double* grad_eps, double* grad_U) {
+  if (!c) return MCD_E_INVALID;
+  int st = need_basis(c);
+  if (st != MCD_OK) return st;
+  if ((st = need_device(c)) != MCD_OK) return st;
+  if (!u || !v) return fail(c, MCD_E_INVALID, "null vector");
+  if (dtype != MCD_F64 && dtype != MCD_F32) return fail(c, MCD_E_INVALID, "dtype must be MCD_F64 or MCD_F32");
+  if (ncols < 1 || ld < ncols) return fail(c, MCD_E_INVALID, "need 1 <= ncols <= ld");
+  return hv_adjoint(c, u, v, ncols, ld, dtype, grad_t, grad_eps, grad_U);
+}
+
 int mcd_diagonal(mcd_ctx* c, double* diag) {
   if (!c) return MCD_E_INVALID;
   int st = need_basis(c);

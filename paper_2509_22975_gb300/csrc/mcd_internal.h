@@ -165,6 +165,10 @@ double tridiag_lowest(const double* a, const double* b, int m, double* vec /*nul
 // leading `rows` rows of the eigenvector matrix X[rows][n]; 0 on success
 int symeig_leading(int n, double* A, double* w, int rows, double* X);
 
+// adjoint of H*v with respect to (t, eps, U) (adjoint.cu)
+int hv_adjoint(mcd_ctx* c, const void* u, const void* v, int ncols, int ld, int dtype, double* grad_t,
+               double* grad_eps, double* grad_U);
+
 // band Lanczos Green function (band.cu)
 int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int n_blocks, double w_t, int dtype,
                        const double* z_re, const double* z_im, int nz, double* G_re, double* G_im,
