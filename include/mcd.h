@@ -61,11 +61,18 @@ typedef enum { MCD_F64 = 0, MCD_F32 = 1 } mcd_dtype;
 /* Options (mcd_set_option). */
 #define MCD_OPT_HV_ALGO 1       /* 0 = two-layout block kernels, in-block
                                    lookup by shared bitmap when n_sites <= 16,
-                                   by binary search otherwise (default);
+                                   by hash table otherwise (default);
                                    1 = plain per-state global binary search;
-                                   2 = two-layout block kernels, binary search */
+                                   2 = two-layout block kernels, binary search;
+                                   3 = two-layout block kernels, hash lookup
+                                   at any n_sites */
 #define MCD_OPT_KERNEL_TIMING 2 /* 1 = record CUDA events around H*v launches */
 #define MCD_OPT_SAMPLER_THREADS 3 /* host threads of the sampler (0 = auto)  */
+#define MCD_OPT_HASH_ITEM 4     /* states per work item of the hash-lookup
+                                   kernels: a power of two in [64, 4096]
+                                   (default 1024).  Blocks of more states are
+                                   split into items that share one table of
+                                   the block in device memory. */
 
 /* Create a context on CUDA device `device` using `cuda_stream` (a
  * cudaStream_t, may be NULL for the legacy default stream).  device = -1

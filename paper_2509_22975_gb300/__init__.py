@@ -19,8 +19,8 @@ from .build import LIB as LIB_PATH, build  # noqa: F401
 MCD_OK, MCD_W_SHORT = 0, 1
 MCD_F64, MCD_F32 = 0, 1
 MCD_SAMPLE_NEW_ONLY = 1
-MCD_OPT_HV_ALGO, MCD_OPT_KERNEL_TIMING, MCD_OPT_SAMPLER_THREADS = 1, 2, 3
-HV_AUTO, HV_PLAIN, HV_SEARCH = 0, 1, 2
+MCD_OPT_HV_ALGO, MCD_OPT_KERNEL_TIMING, MCD_OPT_SAMPLER_THREADS, MCD_OPT_HASH_ITEM = 1, 2, 3, 4
+HV_AUTO, HV_PLAIN, HV_SEARCH, HV_HASH = 0, 1, 2, 3
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mcd.h")
 
 _lib = None

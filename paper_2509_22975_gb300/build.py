@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmcd.so")
-SOURCES = ["mcd_api.cu", "index.cu", "hv.cu", "krylov.cu", "band.cu", "adjoint.cu", "noalloc.cu", "sampler.cpp", "tridiag.cpp",
+SOURCES = ["mcd_api.cu", "index.cu", "hv.cu", "hv_hash.cu", "krylov.cu", "band.cu", "adjoint.cu", "noalloc.cu", "sampler.cpp", "tridiag.cpp",
            "symeig.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
@@ -37,7 +37,7 @@ def _newer(target: str, deps: list[str]) -> bool:
 
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
-    headers = [os.path.join(SRC, h) for h in os.listdir(SRC) if h.endswith(".h")]
+    headers = [os.path.join(SRC, h) for h in os.listdir(SRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "mcd.h"))
     objs = []
     jobs = []

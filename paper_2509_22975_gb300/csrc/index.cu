@@ -234,6 +234,7 @@ static cudaError_t build_layout(mcd_ctx* c, const uint32_t* major, int64_t n, La
   L.n = n;
   L.nblk = int64_t(last_scan) + last_flag;
   L.n_items = (n + kItem - 1) / kItem;
+  L.hash_built = 0;   // hash items describe the previous basis
   block_tables_kernel<<<grid_of(n, T), T, 0, s>>>(major, tmp_flag, tmp_scan, n, L.blk_off,
                                                   L.blk_major, L.item_blk);
   MCD_LAUNCHED(c);
@@ -245,6 +246,7 @@ void free_index(DevIndex& ix) {
   f(ix.words);
   for (Layout* L : {&ix.A, &ix.B}) {
     f(L->minor); f(L->blk_off); f(L->blk_major); f(L->item_blk); f(L->perm);
+    free_hash(*L);
     *L = Layout();
   }
   ix.words = nullptr;

@@ -139,7 +139,7 @@ int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
   if (!c) return MCD_E_INVALID;
   switch (option) {
     case MCD_OPT_HV_ALGO:
-      if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "HV_ALGO must be 0, 1 or 2");
+      if (value < 0 || value > 3) return fail(c, MCD_E_INVALID, "HV_ALGO must be 0, 1, 2 or 3");
       c->hv_algo = int(value);
       return MCD_OK;
     case MCD_OPT_KERNEL_TIMING:
@@ -157,6 +157,11 @@ int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
         }
       }
       c->timing = value ? 1 : 0;
+      return MCD_OK;
+    case MCD_OPT_HASH_ITEM:
+      if (value < 64 || value > 4096 || (value & (value - 1)))
+        return fail(c, MCD_E_INVALID, "HASH_ITEM must be a power of two in [64, 4096]");
+      c->hash_item = int(value);
       return MCD_OK;
     case MCD_OPT_SAMPLER_THREADS:
       if (value < 0 || value > 1024) return fail(c, MCD_E_INVALID, "SAMPLER_THREADS out of range");
@@ -253,6 +258,28 @@ int mcd_set_hamiltonian(mcd_ctx* c, int n, const double* t, const double* eps, c
     } else {
       hp.n_class = 0;
     }
+  }
+  // hop groups: bonds of equal amplitude and equal index distance j - i
+  {
+    hp.n_hg = 0;
+    bool ok = true;
+    for (int b = 0; b < nb && ok; ++b) {
+      const int i = __builtin_ctz(hp.bonds[b].mask);
+      const int j = 31 - __builtin_clz(hp.bonds[b].mask);
+      int g = 0;
+      while (g < hp.n_hg && !(hp.hg_t[g] == hp.bonds[b].t && hp.hg_shift[g] == j - i)) ++g;
+      if (g == hp.n_hg) {
+        if (g == kMaxHopGroups) { ok = false; break; }
+        hp.hg_t[g] = hp.bonds[b].t;
+        hp.hg_hi[g] = hp.bonds[b].t_hi;
+        hp.hg_lo[g] = hp.bonds[b].t_lo;
+        hp.hg_shift[g] = j - i;
+        hp.hg_mask[g] = 0u;
+        ++hp.n_hg;
+      }
+      hp.hg_mask[g] |= 1u << i;
+    }
+    if (!ok) hp.n_hg = 0;
   }
   bool uniform = true;
   for (int i = 1; i < n; ++i)

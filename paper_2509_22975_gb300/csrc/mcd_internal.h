@@ -18,6 +18,7 @@ constexpr int kStageWords = 12288;   // minor words a CTA stages in shared memor
 constexpr int kTimingClasses = 4;
 constexpr int kMaxClasses = 16;      // distinct hopping amplitudes handled by class sums
 constexpr int kMaxPClasses = 32;     // partner classes of the single-column kernel
+constexpr int kMaxHopGroups = 64;    // (amplitude, j - i) groups of the hash kernel
 
 // One undirected bond (i < j, t_ij != 0).  A state of one spin can hop along
 // it iff exactly one of its two sites is occupied; the hop flips both bits.
@@ -62,7 +63,30 @@ struct HamParams {
   double pcls_t[kMaxPClasses];
   const uint2* ptab;                // device [ceil(n_pcls / 4)][2][256]
   const uint2* pflip;               // device [n_pcls][16]: (flip, between) of first endpoint i
+  // Hop groups (any n_sites): bonds (i, i + s) of one amplitude and one index
+  // distance s.  For group g, hg_mask[g] has bit i set for each of its bonds,
+  // so hg_mask[g] & (m ^ (m >> hg_shift[g])) marks the bonds of g along
+  // which a spin word m can hop (exactly one endpoint occupied).
+  int n_hg;                         // 0 = more than kMaxHopGroups groups
+  uint32_t hg_mask[kMaxHopGroups];
+  int hg_shift[kMaxHopGroups];
+  float hg_hi[kMaxHopGroups], hg_lo[kMaxHopGroups];
+  double hg_t[kMaxHopGroups];
 };
+
+// Work item of the hash kernel (hv_hash.cu): layout positions [s0, s1).
+// log2p == 0: whole blocks [b0, b1) whose minor words the CTA hashes in
+// shared memory.  Otherwise a chunk of the single block b0 (b1 = b0 + 1),
+// looked up in that block's table of 2^log2p slots at htab + tab_off, or by
+// binary search when log2p == kHashSearch (block too large for 16-bit slots).
+// Every tabled block also has a one-bit-per-hash membership filter, so most
+// absent targets are rejected by one load.
+struct HItem {
+  uint32_t s0, s1, b0, b1;
+  uint32_t tab_off, log2p;
+  uint32_t flt_off, log2f;   // membership filter of 2^log2f bits at hflt + flt_off
+};
+constexpr uint32_t kHashSearch = 0xFFu;
 
 
 // One of the two orderings of the basis used by the H*v kernels.
@@ -77,6 +101,17 @@ struct Layout {
   uint32_t* blk_major = nullptr; // [nblk]
   uint32_t* item_blk = nullptr;  // [n_items + 1] block of the first state of item i
   uint32_t* perm = nullptr;      // [n] layout position -> basis index (B only)
+  // hash-kernel work items and per-block tables (built on first use)
+  int hash_built = 0;            // item size they were built for (0 = none)
+  int64_t n_hitems = 0;
+  int64_t hitem_cap = 0;
+  HItem* hitems = nullptr;
+  int64_t htab_len = 0;
+  int64_t htab_cap = 0;
+  uint32_t* htab = nullptr;
+  int64_t hflt_len = 0;          // 32-bit words
+  int64_t hflt_cap = 0;
+  uint32_t* hflt = nullptr;
 };
 
 struct DevIndex {
@@ -142,6 +177,7 @@ struct mcd_ctx {
   std::vector<double> last_a, last_b;
   // Options
   int hv_algo = 0;
+  int hash_item = 1024;                // states per work item of the hash kernel
   int timing = 0;
   int sampler_threads = 0;
   mcd::Timing* tm = nullptr;
@@ -185,6 +221,13 @@ int hv_diagonal(mcd_ctx* c, double* out);
 int hv_connections(mcd_ctx* c, int64_t* rows, int64_t* cols, double* vals, int64_t cap,
                    int64_t* nnz);
 int hv_dot_ctas(mcd_ctx* c, int ncols, int dtype);
+
+// hash-lookup H*v (hv_hash.cu): used for n_sites > 16 (or when forced by
+// MCD_OPT_HV_ALGO); both passes, fused <x, y> when dot_out is given
+bool hash_eligible(const mcd_ctx* c);
+int hash_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, double* dot_partials,
+               int max_parts, unsigned int* ticket, double* dot_out);
+void free_hash(Layout& L);
 
 // Lanczos (krylov.cu)
 int lanczos_ground(mcd_ctx* c, int max_iter, double tol, uint64_t seed, int dtype,

@@ -110,13 +110,22 @@ def test_diagonal(which, request):
     assert np.array_equal(d.cpu().numpy(), P.diag)   # integer-valued here: exact
 
 
-@pytest.fixture(params=[pkg.HV_AUTO, pkg.HV_SEARCH], ids=["bitmap", "search"])
+# (algorithm, states per hash work item): the hash kernel at its default item
+# size (1024) and at 64 states per item, where most blocks are split into chunks
+# that share a table in device memory
+ALGOS = [(pkg.HV_AUTO, 1024), (pkg.HV_SEARCH, 1024), (pkg.HV_HASH, 1024), (pkg.HV_HASH, 64)]
+ALGO_IDS = ["auto", "search", "hash", "hash-item64"]
+
+
+@pytest.fixture(params=ALGOS, ids=ALGO_IDS)
 def algo(request):
     return request.param
 
 
 def with_algo(ctx, algo):
-    ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, algo)
+    a, item = algo
+    ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, a)
+    ctx.mcd_set_option(pkg.MCD_OPT_HASH_ITEM, item)
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
@@ -152,11 +161,11 @@ def test_apply_exact_rows_fsum(ring8):
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_plain_kernel_variant(tilted12, dtype):
     w, ctx, B, P = tilted12
-    ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, 1)
+    with_algo(ctx, (pkg.HV_PLAIN, 1024))
     try:
         check_apply(ctx, P, w.lat.t, 2, dtype, seed=99)
     finally:
-        ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, pkg.HV_AUTO)
+        with_algo(ctx, (pkg.HV_AUTO, 1024))
 
 
 def test_single_state_basis(algo):
@@ -194,7 +203,7 @@ def test_oversized_block_uses_global_search():
     B = np.unique(np.concatenate([big] + others))
     ctx = device_ctx(w, basis=B)
     P = H.build(model(w), B)
-    for algo in (pkg.HV_AUTO, pkg.HV_SEARCH):
+    for algo in ALGOS:
         with_algo(ctx, algo)
         for dt in (np.float64, np.float32):
             check_apply(ctx, P, lat.t, 1, dt)
@@ -227,9 +236,83 @@ def test_thirty_two_sites_random_hoppings_and_site_terms():
     assert np.max(np.abs(d.cpu().numpy() - P.diag)) <= 4 * n * U64 * np.max(np.abs(P.diag))
     nnz = ctx.mcd_connections()
     assert nnz == P.nnz_offdiag()
-    for dt in (np.float64, np.float32):
-        check_apply(ctx, P, t, 1, dt, seed=2)
-        check_apply(ctx, P, t, 8, dt, seed=3)
+    for algo in ALGOS:
+        with_algo(ctx, algo)
+        for dt in (np.float64, np.float32):
+            check_apply(ctx, P, t, 1, dt, seed=2)
+            check_apply(ctx, P, t, 8, dt, seed=3)
+
+
+@pytest.fixture(scope="module")
+def rect24():
+    # 6x4 t-t' cluster (24 sites, 11 + 11 electrons): a 60,000-state MC basis
+    w = C.rect24_u8()
+    ctx = device_ctx(w, nf=60000)
+    B = ctx.mcd_get_basis()
+    P = H.build(model(w), B)
+    return w, ctx, B, P
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("ncols,ld,offset", [(1, 1, 0), (3, 3, 0), (24, 24, 0), (48, 48, 0), (5, 8, 0),
+                                             (4, 4, 1), (70, 72, 0)])
+def test_apply_rect24(rect24, dtype, ncols, ld, offset, algo):
+    # more than 16 sites: the default path is the hash kernel
+    w, ctx, B, P = rect24
+    with_algo(ctx, algo)
+    check_apply(ctx, P, w.lat.t, ncols, dtype, ld=ld, offset=offset, seed=11 + ncols)
+
+
+def test_rect24_item_sizes(rect24):
+    # every item size gives the same y (lookups are exact), fp64 bit for bit
+    # across item sizes and against the binary-search kernel
+    w, ctx, B, P = rect24
+    x = torch.from_numpy(random_block(len(B), 2, 5, np.float64)).to(DEV)
+    ys = []
+    for algo in [(pkg.HV_SEARCH, 1024)] + [(pkg.HV_HASH, k) for k in (64, 128, 512, 1024, 4096)]:
+        with_algo(ctx, algo)
+        y = torch.empty_like(x)
+        ctx.mcd_apply(x, y)
+        ys.append(y.cpu().numpy())
+    with_algo(ctx, (pkg.HV_AUTO, 1024))
+    ref = P.sparse() @ x.cpu().numpy()
+    bound = apply_bound(H.apply_abs(P, x.cpu().numpy()), row_terms_bound(n_bonds(w.lat.t)), 2 * U64)
+    for y in ys:
+        assert np.all(np.abs(y - ref) <= bound)
+    for y in ys[2:]:
+        assert np.array_equal(y, ys[1])
+
+
+def test_block_above_table_limit_uses_search():
+    # 20 sites: one up word with all C(20, 10) = 184,756 down words, a block
+    # too large for 16-bit table positions (binary search inside the hash
+    # kernel), plus small blocks
+    n = 20
+    lat = L.ring(n)
+    w = C.Workload("ring20", lat, 4.0, 10, 10, 0, 0.4)
+    dns = np.array(fock.words_with_popcount(n, 10), dtype=np.uint64)
+    ups = fock.words_with_popcount(n, 10)
+    rng = np.random.default_rng(6)
+    parts = [(np.uint64(ups[500]) << np.uint64(n)) | dns]
+    parts += [(np.uint64(ups[k]) << np.uint64(n)) | dns[rng.choice(len(dns), 2000, replace=False)]
+              for k in (1, 499, 501, 7000)]
+    B = np.unique(np.concatenate(parts))
+    ctx = device_ctx(w, basis=B)
+    P = H.build(model(w), B)
+    for algo in [(pkg.HV_AUTO, 1024), (pkg.HV_HASH, 256)]:
+        with_algo(ctx, algo)
+        for dt in (np.float64, np.float32):
+            check_apply(ctx, P, lat.t, 1, dt, seed=4)
+            check_apply(ctx, P, lat.t, 6, dt, seed=5)
+
+
+def test_hash_item_option_errors(ring8):
+    w, ctx, B, P = ring8
+    for bad in (0, 32, 100, 8192):
+        with pytest.raises(pkg.MCDError):
+            ctx.mcd_set_option(pkg.MCD_OPT_HASH_ITEM, bad)
+    with pytest.raises(pkg.MCDError):
+        ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, 4)
 
 
 def test_argument_errors(ring8):

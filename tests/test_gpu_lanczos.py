@@ -66,10 +66,12 @@ def test_tilted12_full_sector_pins():
     assert math.trunc((E - 4.0 * 12) / 12 * 1e4) / 1e4 == -4.5226
 
 
+@pytest.mark.parametrize("algo", [pkg.HV_AUTO, pkg.HV_HASH], ids=["bitmap", "hash"])
 @pytest.mark.parametrize("dtype", [pkg.MCD_F64, pkg.MCD_F32])
-def test_tilted12_mc_basis(dtype):
+def test_tilted12_mc_basis(dtype, algo):
     w = C.tilted12_u8()
     ctx = device_ctx(w)
+    ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, algo)
     r = ctx.mcd_lanczos_ground(800, 1e-12 if dtype == pkg.MCD_F64 else 1e-8, 0, dtype,
                                allow_not_converged=dtype == pkg.MCD_F32)
     E_ref = golden()["tilted12_mc_E0"]
@@ -89,10 +91,31 @@ def test_deterministic_and_plain_variant_agree():
     assert r1["iters"] == r2["iters"] == 60
     assert np.array_equal(a1, a2) and np.array_equal(b1, b2)      # bit-identical reruns
     Es = []
-    for algo in (pkg.HV_PLAIN, pkg.HV_SEARCH, pkg.HV_AUTO):
+    for algo in (pkg.HV_PLAIN, pkg.HV_SEARCH, pkg.HV_HASH, pkg.HV_AUTO):
         ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, algo)
         Es.append(ctx.mcd_lanczos_ground(400, 1e-12, 5, pkg.MCD_F64)["E0"])
     assert max(Es) - min(Es) < 1e-10 * abs(Es[-1])
+
+
+@pytest.mark.parametrize("dtype", [pkg.MCD_F64, pkg.MCD_F32])
+def test_rect24_mc_basis_against_sparse_eigensolver(dtype):
+    # 24 sites (hash-lookup kernels, fused <x, Hx>): E0 of a 60,000-state MC
+    # basis against scipy's Lanczos (ARPACK) on the oracle's explicit H~
+    import scipy.sparse.linalg as sla
+    w = C.rect24_u8()
+    ctx = device_ctx(w, nf=60000)
+    B = ctx.mcd_get_basis()
+    E_ref = float(sla.eigsh(H.build(model(w), B).sparse(), k=1, which="SA", tol=1e-14)[0][0])
+    r = ctx.mcd_lanczos_ground(1000, 1e-12 if dtype == pkg.MCD_F64 else 1e-8, 0, dtype,
+                               allow_not_converged=dtype == pkg.MCD_F32)
+    if dtype == pkg.MCD_F64:
+        assert abs(r["E0"] - E_ref) <= 1e-10 * abs(E_ref)
+    else:
+        assert abs(r["E0"] - E_ref) <= 1e-6
+    ctx.mcd_set_option(pkg.MCD_OPT_HASH_ITEM, 64)   # chunks sharing device tables
+    r2 = ctx.mcd_lanczos_ground(1000, 1e-12 if dtype == pkg.MCD_F64 else 1e-8, 0, dtype,
+                                allow_not_converged=dtype == pkg.MCD_F32)
+    assert abs(r2["E0"] - r["E0"]) <= 1e-12 * abs(E_ref)
 
 
 def test_single_state_breakdown():
