@@ -191,6 +191,44 @@ def traffic_for(kernel_key: str):
     return ent["bytes_per_launch"] if ent.get("hv_cu_sha") == h else None
 
 
+def rect24_hv(pkg, configs, dev, peak, cols=(1, 24, 48), reps=5):
+    """H~V on the 6x4 t-t' cluster (24 sites, 11 + 11 electrons, Monte Carlo
+    basis of 5e7 states, hash-lookup kernels), fp32, each width timed alone
+    with CUDA events after warm-up; X and Y are far larger than L2."""
+    import torch
+    w = configs.rect24_u8()
+    ctx = pkg.Context(dev.index or 0)
+    ctx.mcd_set_hamiltonian(w.lat.t, w.eps, w.U, w.n_up, w.n_dn)
+    t0 = time.perf_counter()
+    ctx.mcd_build_basis(w.seed, w.n_f, w.beta, [w.seed_word()])
+    t_sample = time.perf_counter() - t0
+    info = ctx.mcd_basis_info()
+    n, nnz = info["n_states"], info["nnz_offdiag"]
+    res = {"workload": "rect6x4_tp-0.3_U8_Nup11_Ndn11_mcbasis5e7", "n_states": n, "nnz_offdiag": nnz,
+           "n_up_blocks": info["n_up_blocks"], "sampler_s": t_sample}
+    for L_ in cols:
+        x = torch.randn(n, L_, dtype=torch.float32, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            ctx.mcd_apply(x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.mcd_apply(x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        t_ms = e0.elapsed_time(e1) / reps
+        bytes_ = n * (8 + 2 * L_ * 4)
+        res[f"L{L_}"] = {"ms": t_ms, "Gconn_per_s": nnz * L_ / (t_ms * 1e-3) / 1e9,
+                         "algorithmic_GBps": bytes_ / (t_ms * 1e-3) / 1e9,
+                         "frac_of_peak": bytes_ / (t_ms * 1e-3) / 1e9 / peak}
+        del x, y
+    del ctx
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -203,6 +241,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--hv-cols", type=int, nargs="*", default=[1, 24])
+    ap.add_argument("--no-rect24", action="store_true",
+                    help="skip the 6x4 t-t' (24-site, 5e7-state) H*V measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -336,6 +376,9 @@ def main():
                             "frac_of_peak": bytes_ / (t_ms * 1e-3) / 1e9 / peak}
             del x, y
         out["hv_apply_fp32"] = hv
+
+    if not args.no_rect24:
+        out["hv_apply_rect24_fp32"] = rect24_hv(pkg, configs, dev, peak)
 
     if not args.no_fp64:
         # fp64 form and the plain fp64 path (global binary search kernel), same 200 steps

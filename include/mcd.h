@@ -68,6 +68,12 @@ typedef enum { MCD_F64 = 0, MCD_F32 = 1 } mcd_dtype;
                                    at any n_sites */
 #define MCD_OPT_KERNEL_TIMING 2 /* 1 = record CUDA events around H*v launches */
 #define MCD_OPT_SAMPLER_THREADS 3 /* host threads of the sampler (0 = auto)  */
+#define MCD_OPT_SAMPLER_DEVICE 5 /* where mcd_build_basis runs: 0 = on the
+                                   context's GPU when it has one and every
+                                   nonzero U_i has the same value, else on
+                                   host threads (default); 1 = host threads;
+                                   2 = GPU (MCD_E_INVALID when not possible).
+                                   Both give the same basis, word for word. */
 #define MCD_OPT_HASH_ITEM 4     /* states per work item of the hash-lookup
                                    kernels: a power of two in [64, 4096]
                                    (default 1024).  Blocks of more states are
@@ -107,7 +113,9 @@ int mcd_set_hamiltonian(mcd_ctx* ctx, int n_sites, const double* t, const double
  * SplitMix64 priority), or earlier if no new state appears for 64 steps
  * (returns MCD_W_SHORT).  n_target must not exceed the sector size.  The basis
  * replaces the current one and is indexed on the device (if any). *n_out =
- * basis size. Runs on host threads (MCD_OPT_SAMPLER_THREADS). */
+ * basis size.  Runs on the context's GPU or on host threads
+ * (MCD_OPT_SAMPLER_DEVICE, MCD_OPT_SAMPLER_THREADS); every placement and thread
+ * count gives the same words. */
 int mcd_build_basis(mcd_ctx* ctx, uint64_t seed, int64_t n_target, double beta,
                     const uint64_t* seed_states, int64_t n_seed, int flags, int64_t* n_out);
 

@@ -20,6 +20,8 @@ MCD_OK, MCD_W_SHORT = 0, 1
 MCD_F64, MCD_F32 = 0, 1
 MCD_SAMPLE_NEW_ONLY = 1
 MCD_OPT_HV_ALGO, MCD_OPT_KERNEL_TIMING, MCD_OPT_SAMPLER_THREADS, MCD_OPT_HASH_ITEM = 1, 2, 3, 4
+MCD_OPT_SAMPLER_DEVICE = 5
+SAMPLER_AUTO, SAMPLER_HOST, SAMPLER_DEVICE = 0, 1, 2
 HV_AUTO, HV_PLAIN, HV_SEARCH, HV_HASH = 0, 1, 2, 3
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mcd.h")
 

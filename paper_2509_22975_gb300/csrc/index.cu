@@ -195,7 +195,7 @@ int grid_of(int64_t n, int t) { return int((n + t - 1) / t); }
 }  // namespace
 
 // exclusive scan of n uint32 values (in may equal out)
-static cudaError_t scan_u32(mcd_ctx* c, const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s) {
+cudaError_t scan_u32(mcd_ctx* c, const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
   if (ntiles == 1) {

@@ -163,6 +163,10 @@ int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
         return fail(c, MCD_E_INVALID, "HASH_ITEM must be a power of two in [64, 4096]");
       c->hash_item = int(value);
       return MCD_OK;
+    case MCD_OPT_SAMPLER_DEVICE:
+      if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "SAMPLER_DEVICE must be 0, 1 or 2");
+      c->sampler_where = int(value);
+      return MCD_OK;
     case MCD_OPT_SAMPLER_THREADS:
       if (value < 0 || value > 1024) return fail(c, MCD_E_INVALID, "SAMPLER_THREADS out of range");
       c->sampler_threads = int(value);
@@ -402,6 +406,17 @@ int mcd_build_basis(mcd_ctx* c, uint64_t seed, int64_t n_target, double beta, co
   if (n_target < 1 || double(n_target) > sector_size(c->n, c->n_up, c->n_dn))
     return fail(c, MCD_E_INVALID, "n_target must be in [1, sector size]");
   if (n_target > 0x7FFFFFFF) return fail(c, MCD_E_INVALID, "n_target above 2^31 - 1");
+  const bool dev_ok = has_device(c) && device_sampler_eligible(c);
+  if (c->sampler_where == 2 && !dev_ok)
+    return fail(c, MCD_E_INVALID,
+                has_device(c) ? "device sampler needs every nonzero U_i equal" : "device sampler needs a device");
+  if (dev_ok && c->sampler_where != 1) {
+    int st = need_device(c);
+    if (st != MCD_OK) return st;
+    st = sample_basis_device(c, seed, n_target, beta, seed_states, n_seed, flags, n_out);
+    if (st == MCD_W_SHORT) c->err = "sampler stopped early: no new states";
+    return st;
+  }
   std::vector<uint64_t> F;
   int st;
   try {

@@ -180,6 +180,7 @@ struct mcd_ctx {
   int hash_item = 1024;                // states per work item of the hash kernel
   int timing = 0;
   int sampler_threads = 0;
+  int sampler_where = 0;                // 0 auto, 1 host threads, 2 device
   mcd::Timing* tm = nullptr;
 };
 
@@ -210,8 +211,16 @@ int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int 
                        const double* z_re, const double* z_im, int nz, double* G_re, double* G_im,
                        int64_t* dim_plus, int64_t* dim_minus);
 
+// device sampler (sampler_gpu.cu): same result as sample_basis; applies when
+// every nonzero U_i has the same value; installs the basis on the device
+bool device_sampler_eligible(const mcd_ctx* c);
+int sample_basis_device(mcd_ctx* c, uint64_t seed, int64_t n_target, double beta, const uint64_t* seeds,
+                        int64_t n_seed, int flags, int64_t* n_out);
+
 // device index (index.cu)
 int build_index(mcd_ctx* c, const uint64_t* words, int64_t n, bool on_device);
+// exclusive scan of n uint32 values (in may equal out), stream-ordered
+cudaError_t scan_u32(mcd_ctx* c, const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
 void free_index(DevIndex& ix);
 
 // H*v (hv.cu)

@@ -154,3 +154,20 @@ def test_sampler_argument_errors():
         with pytest.raises(pkg.MCDError) as e:
             ctx.mcd_build_basis(*args)
         assert e.value.status == code
+
+
+def test_sampler_placement_option_on_host_context():
+    # a host-only context samples on host threads under the default; asking
+    # for the device is an error, not a silent change of placement
+    w = C.ring8_u4()
+    ctx = host_ctx(w)
+    ctx.mcd_set_option(pkg.MCD_OPT_SAMPLER_DEVICE, pkg.SAMPLER_AUTO)
+    ctx.mcd_build_basis(w.seed, 500, w.beta, [w.seed_word()])
+    assert len(ctx.mcd_get_basis()) == 500
+    ctx.mcd_set_option(pkg.MCD_OPT_SAMPLER_DEVICE, pkg.SAMPLER_DEVICE)
+    with pytest.raises(pkg.MCDError) as e:
+        ctx.mcd_build_basis(w.seed, 500, w.beta, [w.seed_word()])
+    assert e.value.status == -1
+    for bad in (-1, 3):
+        with pytest.raises(pkg.MCDError):
+            ctx.mcd_set_option(pkg.MCD_OPT_SAMPLER_DEVICE, bad)
