@@ -186,9 +186,10 @@ def traffic_for(kernel_key: str):
     ent = d.get(kernel_key)
     if not ent:
         return None
-    src = os.path.join(ROOT, "paper_2509_22975_gb300", "csrc", "hv.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return ent["bytes_per_launch"] if ent.get("hv_cu_sha") == h else None
+    h = hashlib.sha256()
+    for f in ("hv.cu", "hv_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2509_22975_gb300", "csrc", f), "rb").read())
+    return ent["bytes_per_launch"] if ent.get("kernel_src_sha") == h.hexdigest()[:16] else None
 
 
 def rect24_hv(pkg, configs, dev, peak, cols=(1, 24, 48), reps=5):
@@ -322,7 +323,7 @@ def main():
     tb, ta = traffic_for("hv_pass_B_square16_fp32_L1"), traffic_for("hv_pass_A_square16_fp32_L1")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tb + ta) if (tb is not None and ta is not None) else None,
-                "kernel": "H~v pair (hv_block_kernel pass B + pass A), one application",
+                "kernel": "H~v pair (hv_l1_kernel pass B + pass A), one application",
                 "algorithmic_bytes": alg_bytes, "peak_source": peak_src,
                 "mean_ms": {"pass_B": tB, "pass_A": tA, "krylov_update": tU},
                 "share_of_step": {"pass_B": kms[0] / args.steps / ms, "pass_A": kms[1] / args.steps / ms,
