@@ -225,6 +225,36 @@ int mcd_band_lanczos_green(mcd_ctx* ctx, const int* orb_site, const int* orb_spi
  * iteration cap is reached. */
 int mcd_symeig(int n, const double* A, double* w, int rows, double* X);
 
+/* Batches of small models (embedding calculations: many impurity models,
+ * each with its own Hamiltonian and Monte Carlo basis of its own size).
+ * ctxs[n_inst]: contexts on one device, each with a Hamiltonian of at most 16
+ * sites and an installed basis; they are read, not modified (except for
+ * launch counts and error text, which go to ctxs[0]).  Errors are reported on
+ * ctxs[0]: MCD_E_INVALID (bad arguments, more than 16 sites, contexts on
+ * different devices), MCD_E_NODEVICE, MCD_E_STATE (no basis), MCD_E_OOM.
+ *
+ * mcd_batch_apply: y_i = H~_i x_i for every instance (App. B projection, as
+ * mcd_apply), single column.  x, y: device arrays of sum_i N_i elements of
+ * dtype, instance i at offset N_0 + ... + N_{i-1}; x and y must not overlap.
+ * All instances run in one persistent launch per pass that pulls (instance,
+ * work item) units from a device queue; the launch grid is chosen by timing
+ * candidates on the first batch of a given size. */
+int mcd_batch_apply(mcd_ctx* const* ctxs, int n_inst, const void* x, void* y, int dtype);
+/* App. B Lanczos ground state of every instance, all instances advancing in
+ * lockstep (one launch per phase for the batch; the launches of 16 steps are
+ * captured once in a CUDA graph and replayed).  Each instance stops when its
+ * residual estimate b_{m+1} |e_m^T y| < tol max(1, |E0|) or at max_iter
+ * (1 <= max_iter <= 100000).  Start vectors as mcd_lanczos_ground with the
+ * same seed.  All Krylov vectors are kept (MCD_E_OOM if they do not fit).
+ * E0: host [n_inst]; iters, residual: host [n_inst] or NULL.  psi: NULL or
+ * host [n_inst] of device pointers (each NULL or N_i elements of dtype) that
+ * receive the normalised Ritz vectors.  The MCD_F32 form returns each
+ * instance's fp64 Rayleigh quotient of its Ritz vector.  Status:
+ * MCD_E_NOT_CONVERGED if some instance reached max_iter with tol > 0 (E0 is
+ * still filled), MCD_E_BREAKDOWN on a non-finite coefficient. */
+int mcd_batch_lanczos_ground(mcd_ctx* const* ctxs, int n_inst, int max_iter, double tol, uint64_t seed,
+                             int dtype, double* E0, int* iters, double* residual, void* const* psi);
+
 /* Lanczos coefficients of the last mcd_lanczos_ground: a[cap], b[cap]
  * (b[0] = 0); *m = number of steps. Host arrays. */
 int mcd_lanczos_coeffs(const mcd_ctx* ctx, double* a, double* b, int cap, int* m);

@@ -60,6 +60,10 @@ _SIGS = {
                                               ctypes.c_int, c_dp, c_dp, c_i64p, c_i64p]),
     "mcd_symeig": (ctypes.c_int, [ctypes.c_int, c_dp, c_dp, ctypes.c_int, c_dp]),
     "mcd_hv_adjoint": (ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_dp, c_dp, c_dp]),
+    "mcd_batch_apply": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, c_vp, c_vp, ctypes.c_int]),
+    "mcd_batch_lanczos_ground": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_uint64, ctypes.c_int, c_dp, ctypes.POINTER(ctypes.c_int),
+                                                c_dp, ctypes.POINTER(c_vp)]),
 }
 
 
@@ -101,6 +105,51 @@ def mcd_symeig(A, rows: int | None = None):
     if st != MCD_OK:
         raise MCDError(st, "mcd_symeig")
     return w, X
+
+
+def _ctx_array(ctxs):
+    arr = (c_vp * len(ctxs))()
+    for i, c in enumerate(ctxs):
+        arr[i] = c.h
+    return arr
+
+
+def _batch_check(ctxs, st, name, ok=(0,)):
+    if st not in ok:
+        msg = lib().mcd_last_error(ctxs[0].h) if ctxs else b""
+        raise MCDError(st, f"{name}: {(msg or b'').decode()}")
+    return st
+
+
+def mcd_batch_apply(ctxs, x, y):
+    """y_i = H~_i x_i for every context; x, y: 1-D device tensors holding the
+    instances' vectors back to back (float32 or float64)."""
+    for c in ctxs:
+        c._sync_stream()
+    st = lib().mcd_batch_apply(_ctx_array(ctxs), len(ctxs), _ptr(x), _ptr(y), _dtype_code(x))
+    return _batch_check(ctxs, st, "mcd_batch_apply")
+
+
+def mcd_batch_lanczos_ground(ctxs, max_iter: int, tol: float, seed: int, dtype: int, psi=None,
+                             allow_not_converged: bool = False):
+    """Lanczos ground states of all contexts in lockstep; returns dict with
+    E0, iters, residual (numpy arrays) and status.  psi: None or a list of
+    device tensors (or None entries) receiving the normalised Ritz vectors."""
+    for c in ctxs:
+        c._sync_stream()
+    n = len(ctxs)
+    E0 = np.zeros(n)
+    it = (ctypes.c_int * n)()
+    res = np.zeros(n)
+    parr = None
+    if psi is not None:
+        parr = (c_vp * n)()
+        for i, p in enumerate(psi):
+            parr[i] = _ptr(p) or None
+    st = lib().mcd_batch_lanczos_ground(_ctx_array(ctxs), n, max_iter, tol, seed, dtype, E0.ctypes.data_as(c_dp), it,
+                                        res.ctypes.data_as(c_dp), parr)
+    _batch_check(ctxs, st, "mcd_batch_lanczos_ground", ok=(0, -5) if allow_not_converged else (0,))
+    return {"E0": E0, "iters": np.array(list(it)), "residual": res, "status": st}
 
 
 def _ptr(t) -> int:

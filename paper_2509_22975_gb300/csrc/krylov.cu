@@ -181,12 +181,12 @@ __global__ void axpy_kernel(T* psi, const T* s, int64_t n, double coef) {
     psi[k] += c * s[k];
 }
 
-// psi[k] = sum_{j < m} coef[j] V[j][k] in fp64 (V: m stored vectors of n)
+// psi[k] = sum_{j < m} coef[j] V[j][k] in fp64 (V: m stored vectors, stride ld)
 template <typename T>
-__global__ void combine_kernel(double* psi, const T* V, int64_t n, int m, const double* coef) {
+__global__ void combine_kernel(double* psi, const T* V, int64_t n, int64_t ld, int m, const double* coef) {
   for (int64_t k = int64_t(blockIdx.x) * kThreads + threadIdx.x; k < n; k += int64_t(gridDim.x) * kThreads) {
     double acc = 0.0;
-    for (int j = 0; j < m; ++j) acc = fma(__ldg(coef + j), double(V[int64_t(j) * n + k]), acc);
+    for (int j = 0; j < m; ++j) acc = fma(__ldg(coef + j), double(V[int64_t(j) * ld + k]), acc);
     psi[k] = acc;
   }
 }
@@ -249,15 +249,17 @@ int ensure_work(mcd_ctx* c, int dtype, int max_iter) {
   // second pass for the Ritz vector); else two rotating slots
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  const size_t held = w.V ? size_t(w.nvec) * size_t(w.n) * (w.dtype == MCD_F64 ? 8 : 4) : 0;
+  const size_t held = w.V ? size_t(w.nvec) * size_t(w.ld) * (w.dtype == MCD_F64 ? 8 : 4) : 0;
   const bool want_store = double(max_iter + 1) * double(n) * double(es) <= 0.5 * double(free_b + held);
   const int nvec = want_store ? max_iter + 1 : 2;
   if (w.n == n && w.dtype == dtype && w.scal_cap >= cap && w.max_ctas >= ctas && w.nvec >= nvec &&
       w.stored == want_store)
     return MCD_OK;
   free_lanczos(w);
+  // slots start on 16-byte boundaries (the update kernel moves 16-byte vectors)
+  const int64_t ld = (n + 3) & ~int64_t(3);
   cudaError_t e = cudaMalloc(&w.W, size_t(n) * es + 64);
-  if (e == cudaSuccess) e = cudaMalloc(&w.V, size_t(nvec) * size_t(n) * es + 64);
+  if (e == cudaSuccess) e = cudaMalloc(&w.V, size_t(nvec) * size_t(ld) * es + 64);
   if (e == cudaSuccess && dtype == MCD_F32) e = cudaMalloc(&w.psi64, size_t(n) * 8 + 64);
   if (e == cudaSuccess && dtype == MCD_F32) e = cudaMalloc(&w.w64, size_t(n) * 8 + 64);
   if (e == cudaSuccess) e = cudaMalloc(&w.coef, sizeof(double) * cap);
@@ -270,6 +272,7 @@ int ensure_work(mcd_ctx* c, int dtype, int max_iter) {
     return cuda_fail(c, e, "Lanczos workspace");
   }
   w.n = n;
+  w.ld = ld;
   w.dtype = dtype;
   w.nvec = nvec;
   w.stored = want_store;
@@ -291,7 +294,7 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
   T* W = static_cast<T*>(w.W);
   const bool fp32 = sizeof(T) == 4;
   // Krylov vector s_j: its own slot when all are stored, else slot j % 2
-  auto vec = [&](int j) -> T* { return V + int64_t(w.stored ? j : (j & 1)) * n; };
+  auto vec = [&](int j) -> T* { return V + int64_t(w.stored ? j : (j & 1)) * w.ld; };
 
   auto fresh_start = [&]() -> cudaError_t {
     start_kernel<T><<<vg, kThreads, 0, s>>>(vec(0), n, key, w.partials, w.ticket, w.scal + sl.nrm2(0));
@@ -381,7 +384,7 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
     e = cudaMemcpyAsync(w.coef, coef.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "Ritz coefficients");
     if (fp32 || sizeof(T) == 8) {
-      combine_kernel<T><<<vg, kThreads, 0, s>>>(p64, V, n, m, w.coef);
+      combine_kernel<T><<<vg, kThreads, 0, s>>>(p64, V, n, w.ld, m, w.coef);
       MCD_LAUNCHED(c);
     }
   } else {

@@ -605,6 +605,23 @@ int mcd_symeig(int n, const double* A, double* w, int rows, double* X) {
   return symeig_leading(n, work.data(), w, X ? rows : 0, X) == 0 ? MCD_OK : MCD_E_NOT_CONVERGED;
 }
 
+int mcd_batch_apply(mcd_ctx* const* ctxs, int n_inst, const void* x, void* y, int dtype) {
+  try {
+    return batch_apply(ctxs, n_inst, x, y, dtype);
+  } catch (const std::bad_alloc&) {
+    return ctxs && n_inst > 0 && ctxs[0] ? fail(ctxs[0], MCD_E_OOM, "batch: out of host memory") : MCD_E_OOM;
+  }
+}
+
+int mcd_batch_lanczos_ground(mcd_ctx* const* ctxs, int n_inst, int max_iter, double tol, uint64_t seed, int dtype,
+                             double* E0, int* iters, double* residual, void* const* psi) {
+  try {
+    return batch_lanczos_ground(ctxs, n_inst, max_iter, tol, seed, dtype, E0, iters, residual, psi);
+  } catch (const std::bad_alloc&) {
+    return ctxs && n_inst > 0 && ctxs[0] ? fail(ctxs[0], MCD_E_OOM, "batch: out of host memory") : MCD_E_OOM;
+  }
+}
+
 int mcd_lanczos_coeffs(const mcd_ctx* c, double* a, double* b, int cap, int* m) {
   if (!c || !m) return MCD_E_INVALID;
   *m = int(c->last_a.size());

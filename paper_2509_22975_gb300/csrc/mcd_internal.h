@@ -126,7 +126,8 @@ struct LanczosWork {
   int64_t n = 0;
   int dtype = -1;
   void* W = nullptr;             // H s_n
-  void* V = nullptr;             // Krylov vectors: nvec slots of n elements
+  void* V = nullptr;             // Krylov vectors: nvec slots of ld elements
+  int64_t ld = 0;                // slot stride: n rounded up to 4 (16-byte aligned slots)
   int nvec = 0;                  // max_iter + 1 (all stored) or 2 (rotating)
   bool stored = false;
   double* psi64 = nullptr;       // fp64 Ritz vector and H psi (fp32 form polish)
@@ -216,6 +217,11 @@ int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int 
 bool device_sampler_eligible(const mcd_ctx* c);
 int sample_basis_device(mcd_ctx* c, uint64_t seed, int64_t n_target, double beta, const uint64_t* seeds,
                         int64_t n_seed, int flags, int64_t* n_out);
+
+// batches of contexts (batch.cu)
+int batch_apply(mcd_ctx* const* ctxs, int n, const void* x, void* y, int dtype);
+int batch_lanczos_ground(mcd_ctx* const* ctxs, int n, int max_iter, double tol, uint64_t seed, int dtype,
+                         double* E0, int* iters, double* resid, void* const* psi);
 
 // device index (index.cu)
 int build_index(mcd_ctx* c, const uint64_t* words, int64_t n, bool on_device);

@@ -151,3 +151,19 @@ def test_square16_full_size_fp32_vs_fp64():
     r32 = ctx.mcd_lanczos_ground(200, 0.0, 0, pkg.MCD_F32)
     assert abs(r32["E0"] - r64["E0"]) < 1e-6, (r32, r64)
     assert r64["E0"] < golden()["square16_mc65536_E0"]
+
+
+@pytest.mark.parametrize("nf", [1999, 2001, 2002, 1997])
+@pytest.mark.parametrize("dtype", [pkg.MCD_F64, pkg.MCD_F32])
+def test_bases_of_every_size_mod_four(nf, dtype):
+    # stored Krylov vectors start on 16-byte boundaries whatever N_f is (the
+    # update kernel moves 16-byte vectors); E0 against the dense oracle
+    w = C.ring8_u4()
+    ctx = device_ctx(w, nf=nf)
+    B = ctx.mcd_get_basis()
+    assert len(B) == nf
+    E_ref = LZ.dense_ground(H.build(model(w), B).dense())[0]
+    psi = torch.empty(nf, dtype=torch.float64 if dtype == pkg.MCD_F64 else torch.float32, device=DEV)
+    r = ctx.mcd_lanczos_ground(800, 1e-12 if dtype == pkg.MCD_F64 else 1e-8, 0, dtype, psi=psi,
+                               allow_not_converged=dtype == pkg.MCD_F32)
+    assert abs(r["E0"] - E_ref) <= (1e-10 * abs(E_ref) if dtype == pkg.MCD_F64 else 1e-6)
