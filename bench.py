@@ -192,6 +192,56 @@ def traffic_for(kernel_key: str):
     return ent["bytes_per_launch"] if ent.get("kernel_src_sha") == h.hexdigest()[:16] else None
 
 
+def impurity_batch(pkg, dev, n_inst=256, steps=400, tol=1e-6):
+    """256 impurity models (2x2 plaquette + 8 bath sites, Monte Carlo bases
+    log-uniform in [1e3, 1e5] states): fp32 Lanczos of every instance to a
+    relative residual of 1e-6 (the fp32 form's floor; at most 400 steps),
+    batched (persistent launches, CUDA-graph replay) against the same
+    contexts solved one after another; both timed after one untimed run,
+    contexts and bases built beforehand."""
+    import numpy as np
+    import torch
+    from workloads import impurity as IM
+    ms = IM.batch(n_inst)
+    ctxs = []
+    for m in ms:
+        c = pkg.Context(dev.index or 0)
+        c.mcd_set_hamiltonian(m.t, m.eps, m.U_sites, m.n_up, m.n_dn)
+        c.mcd_build_basis(m.seed, m.n_f, m.beta, [m.seed_word()])
+        ctxs.append(c)
+    n_states = sum(c.mcd_basis_info(nnz=False)["n_states"] for c in ctxs)
+    nnz_of = [c.mcd_basis_info()["nnz_offdiag"] for c in ctxs]
+    run = dict(allow_not_converged=True)
+    pkg.mcd_batch_lanczos_ground(ctxs, steps, tol, 0, pkg.MCD_F32, **run)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = pkg.mcd_batch_lanczos_ground(ctxs, steps, tol, 0, pkg.MCD_F32, **run)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    for c in ctxs[:4]:
+        c.mcd_lanczos_ground(steps, tol, 0, pkg.MCD_F32, **run)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [c.mcd_lanczos_ground(steps, tol, 0, pkg.MCD_F32, **run) for c in ctxs]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    E_seq = np.asarray([q["E0"] for q in seq])
+    conns = int(sum(z * int(i) for z, i in zip(nnz_of, r["iters"])))
+    out = {"workload": "impurity_batch256_plaquette4_bath8_mcbasis1e3to1e5_lanczos_tol1e-6_fp32",
+           "n_inst": n_inst, "n_states": n_states, "nnz_offdiag": int(sum(nnz_of)),
+           "batched_s": t_batch, "sequential_s": t_seq, "speedup": t_seq / t_batch,
+           "batched_Gconn_per_s": conns / t_batch / 1e9, "sequential_Gconn_per_s": conns / t_seq / 1e9,
+           "max_dE0_batched_vs_sequential": float(np.max(np.abs(E_seq - r["E0"]))),
+           "lanczos_steps": {"batched_min": int(np.min(r["iters"])), "batched_max": int(np.max(r["iters"])),
+                             "batched_total": int(np.sum(r["iters"])),
+                             "sequential_total": int(sum(q["iters"] for q in seq))},
+           "tol": tol,
+           "timing": "wall clock around each call with device synchronisation; includes host tridiagonal solves"}
+    for c in ctxs:
+        c.close()
+    return out
+
+
 def rect24_hv(pkg, configs, dev, peak, cols=(1, 24, 48), reps=5):
     """H~V on the 6x4 t-t' cluster (24 sites, 11 + 11 electrons, Monte Carlo
     basis of 5e7 states, hash-lookup kernels), fp32, each width timed alone
@@ -242,6 +292,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--hv-cols", type=int, nargs="*", default=[1, 24])
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-impurity batch measurement")
     ap.add_argument("--no-rect24", action="store_true",
                     help="skip the 6x4 t-t' (24-site, 5e7-state) H*V measurements")
     args = ap.parse_args()
@@ -380,6 +431,8 @@ def main():
 
     if not args.no_rect24:
         out["hv_apply_rect24_fp32"] = rect24_hv(pkg, configs, dev, peak)
+    if not args.no_batch:
+        out["impurity_batch"] = impurity_batch(pkg, dev)
 
     if not args.no_fp64:
         # fp64 form and the plain fp64 path (global binary search kernel), same 200 steps

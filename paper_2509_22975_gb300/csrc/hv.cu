@@ -29,7 +29,8 @@ constexpr int kThreads = 256;
 constexpr int kBitmapMaxSites = 16;            // 2^16-bit bitmap = 8 KiB of shared memory
 constexpr int kStageXBytes = 52 * 1024;        // x staging area of the bitmap kernel
 constexpr int kStageX1Bytes = 20 * 1024;       // x staging area of the single-column kernel
-constexpr int kStageXcBytes = 72 * 1024;       // shared memory of the multi-column kernel
+constexpr int kStageXcBytes = 52 * 1024;       // shared memory of the multi-column kernel
+constexpr int kLcCap = 48;                     // found hops per state in its list
 
 // ---------------------------------------------------------------------------------
 template <typename T, int VEC, int G, bool PASS_A, bool DOT>
@@ -666,10 +667,13 @@ __global__ void __launch_bounds__(kThreads) hv_l1_kernel(const HvArgs a, const H
 // Multi-column variant (H~V, band Lanczos).  Rounds of 256 states; in phase
 // 1 one thread per state enumerates its active hops from the partner classes
 // and looks them up once, writing each found target as a 2-byte record
-// (block-local index | sign << 14 | class-half << 15) into a shared list per
-// class pair (at most 32 records: one per bit of the pair's mask).  In phase
-// 2 groups of G lanes read the lists of their states and gather and sum the
-// VEC columns each lane owns (from staged block rows when they fit).
+// (block-local index | sign << 14 | class-half << 15) into one shared list
+// per state, in class-pair order, with the list's end after each pair (at
+// most kLcCap records; a state with more is flagged and its hops are found
+// again by its lanes in phase 2).  In phase 2 groups of G lanes read the
+// lists of their states and gather and sum the VEC columns each lane owns
+// (from staged block rows when they fit), four rows in flight.  The compact
+// lists keep a CTA at ~52 KiB of shared memory, four CTAs per SM.
 template <typename T, int VEC, int G, bool PASS_A>
 __global__ void __launch_bounds__(kThreads) hv_lc_kernel(const HvArgs a, const HamParams hp) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -679,8 +683,9 @@ __global__ void __launch_bounds__(kThreads) hv_lc_kernel(const HvArgs a, const H
   uint2* s_pt = reinterpret_cast<uint2*>(s_dyn + a.off_pt);
   uint2* bm = reinterpret_cast<uint2*>(s_dyn + a.off_bm);
   T* xs = reinterpret_cast<T*>(s_dyn + a.off_xs);
-  uint16_t* lists = reinterpret_cast<uint16_t*>(s_dyn + a.off_list);   // [256][npairs][32]
-  uint8_t* cnts = reinterpret_cast<uint8_t*>(s_dyn + a.off_cnt);        // [256][npairs]
+  uint16_t* lists = reinterpret_cast<uint16_t*>(s_dyn + a.off_list);   // [256][kLcCap]
+  uint8_t* cnts = reinterpret_cast<uint8_t*>(s_dyn + a.off_cnt);        // [256][npairs] list ends
+  uint8_t* ovf = cnts + kThreads * ((hp.n_pcls + 1) / 2);                // [256] list overflowed
   const Layout& L = a.L;
   const int item = blockIdx.x;
   const int64_t k0 = int64_t(item) * kItem;
@@ -713,7 +718,7 @@ __global__ void __launch_bounds__(kThreads) hv_lc_kernel(const HvArgs a, const H
   const int col = g * VEC;
   const int cvalid = ncols - col;
   using C = ChunkOf<T, VEC>;
-  uint16_t* mylist = lists + threadIdx.x * npairs * 32;
+  uint16_t* mylist = lists + threadIdx.x * kLcCap;
   uint8_t* mycnt = cnts + threadIdx.x * npairs;
 
   for (uint32_t blk = s_b0; blk <= s_b1; ++blk) {
@@ -742,6 +747,7 @@ __global__ void __launch_bounds__(kThreads) hv_lc_kernel(const HvArgs a, const H
       // phase 1: lookups, one thread per state
       {
         const int k = r0 + threadIdx.x;
+        int nf = 0;
         if (k < hi) {
           const uint32_t m = L.minor[k];
           const uint32_t mm = m | (m << 16);
@@ -755,30 +761,35 @@ __global__ void __launch_bounds__(kThreads) hv_lc_kernel(const HvArgs a, const H
               const uint32_t pp = h ? (t0.y | t1.y) : (t0.x | t1.x);
               uint32_t act = (mm ^ pp) & (hp.pfirst[c] | (pair ? hp.pfirst[c + 1] << 16 : 0u));
               const uint2* fl = pflip + c * 16;
-              uint16_t* out = mylist + (c >> 1) * 32;
-              int nf = 0;
               while (act) {
                 const int i1 = __ffs(act) - 1;
                 act &= act - 1u;
                 const uint2 f1 = fl[i1];
                 const int q1 = l1_find(bm, m ^ f1.x);
-                if (q1 >= 0)
-                  out[nf++] = uint16_t(q1 | ((__popc(m & f1.y) & 1u) << 14) | ((i1 >> 4) << 15));
+                if (q1 >= 0) {
+                  if (nf < kLcCap)
+                    mylist[nf] = uint16_t(q1 | ((__popc(m & f1.y) & 1u) << 14) | ((i1 >> 4) << 15));
+                  ++nf;
+                }
               }
-              mycnt[c >> 1] = uint8_t(nf);
+              mycnt[c >> 1] = uint8_t(nf < kLcCap ? nf : kLcCap);
             }
           }
         } else {
           for (int pi = 0; pi < npairs; ++pi) mycnt[pi] = 0;
         }
+        ovf[threadIdx.x] = nf > kLcCap ? 1 : 0;
       }
       __syncthreads();
       // phase 2: gathers, G lanes per state
       const int ns = (hi - r0 < kThreads) ? hi - r0 : kThreads;
       for (int t = group; t < ns; t += kGroups) {
         const int k = r0 + t;
-        const uint16_t* lt = lists + t * npairs * 32;
+        const uint16_t* lt = lists + t * kLcCap;
         const uint8_t* ct = cnts + t * npairs;
+        const bool over = ovf[t] != 0;
+        const uint32_t mk = over ? L.minor[k] : 0u;
+        const uint32_t mmk = mk | (mk << 16);
         Acc<T> acc[VEC];
 #pragma unroll
         for (int u = 0; u < VEC; ++u) acc[u].zero();
@@ -788,29 +799,71 @@ __global__ void __launch_bounds__(kThreads) hv_lc_kernel(const HvArgs a, const H
           T s0[VEC], s1[VEC];
 #pragma unroll
           for (int u = 0; u < VEC; ++u) s0[u] = s1[u] = T(0);
-          const int nf = ct[pi];
-          for (int j = 0; j < nf; ++j) {
-            const uint32_t e = lt[pi * 32 + j];
-            const int q = int(e & 0x3FFFu);
-            if (cvalid <= 0) continue;
-            T xv[VEC];
-            if (staged) {
+          const int jb = pi ? int(ct[pi - 1]) : 0;
+          const int nf = (cvalid > 0 && !over) ? int(ct[pi]) : 0;
+          if (over && cvalid > 0) {
+            // the state's list overflowed: find this pair's hops again, in
+            // the order phase 1 uses
+            const int gi = c >> 2, h = (c >> 1) & 1;
+            const uint2 t0 = ptab[gi * 512 + (mk & 255u)];
+            const uint2 t1 = ptab[gi * 512 + 256 + (mk >> 8)];
+            const uint32_t pp = h ? (t0.y | t1.y) : (t0.x | t1.x);
+            uint32_t act = (mmk ^ pp) & (hp.pfirst[c] | (pair ? hp.pfirst[c + 1] << 16 : 0u));
+            const uint2* fl = pflip + c * 16;
+            while (act) {
+              const int i1 = __ffs(act) - 1;
+              act &= act - 1u;
+              const uint2 f1 = fl[i1];
+              const int q = l1_find(bm, mk ^ f1.x);
+              if (q < 0) continue;
+              T xv[VEC];
+              if (staged) {
 #pragma unroll
-              for (int u = 0; u < VEC; ++u) xv[u] = xs[q * ncp + col + u];
-            } else {
-              const int64_t row = PASS_A ? int64_t(bs + q) : int64_t(L.perm[bs + q]);
-              C::load(x + row * ld + col, cvalid, xv);
+                for (int u = 0; u < VEC; ++u) xv[u] = xs[q * ncp + col + u];
+              } else {
+                const int64_t row = PASS_A ? int64_t(bs + q) : int64_t(L.perm[bs + q]);
+                C::load(x + row * ld + col, cvalid, xv);
+              }
+              const bool neg = __popc(mk & f1.y) & 1u;
+              if (i1 >> 4) {
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) s1[u] += neg ? -xv[u] : xv[u];
+              } else {
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) s0[u] += neg ? -xv[u] : xv[u];
+              }
             }
-            if (e & 0x4000u) {
+          }
+          // rows of up to four hits are loaded before any is added (four
+          // independent loads in flight); the sums keep the list order
+          for (int j0 = jb; j0 < nf; j0 += 4) {
+            uint32_t e[4];
+            T xv[4][VEC];
 #pragma unroll
-              for (int u = 0; u < VEC; ++u) xv[u] = -xv[u];
+            for (int h = 0; h < 4; ++h) e[h] = j0 + h < nf ? uint32_t(lt[j0 + h]) : 0u;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              if (j0 + h >= nf) break;
+              const int q = int(e[h] & 0x3FFFu);
+              if (staged) {
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) xv[h][u] = xs[q * ncp + col + u];
+              } else {
+                const int64_t row = PASS_A ? int64_t(bs + q) : int64_t(L.perm[bs + q]);
+                C::load(x + row * ld + col, cvalid, xv[h]);
+              }
             }
-            if (e & 0x8000u) {
 #pragma unroll
-              for (int u = 0; u < VEC; ++u) s1[u] += xv[u];
-            } else {
+            for (int h = 0; h < 4; ++h) {
+              if (j0 + h >= nf) break;
+              const bool neg = e[h] & 0x4000u;
+              if (e[h] & 0x8000u) {
 #pragma unroll
-              for (int u = 0; u < VEC; ++u) s0[u] += xv[u];
+                for (int u = 0; u < VEC; ++u) s1[u] += neg ? -xv[h][u] : xv[h][u];
+              } else {
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) s0[u] += neg ? -xv[h][u] : xv[h][u];
+              }
             }
           }
 #pragma unroll
@@ -1051,16 +1104,17 @@ cudaError_t launch_pair(mcd_ctx* c, const void* x, void* y, int ncols, int ld, d
   }
   const bool lc = bitmap && !l1 && c->hp->n_pcls > 0 && c->hp->n_pcls <= 8 && !partials && ncols <= G * VEC;
   if (lc) {
-    // layout: [ptab + flips][bm: nw uint2][lists: 256 x npairs x 32 u16][counts: 256 x npairs][xs]
+    // layout: [ptab + flips][bm: nw uint2][lists: 256 x kLcCap u16][list ends: 256 x npairs]
+    //         [overflow flags: 256][xs]
     const int ngp = (c->hp->n_pcls + 3) / 4;
     const int npairs = (c->hp->n_pcls + 1) / 2;
     a.off_pt = 0;
     a.off_bm = (ngp * 512 + c->hp->n_pcls * 16) * 8;
     a.off_list = a.off_bm + 8 * a.nw;
-    a.off_cnt = a.off_list + kThreads * npairs * 32 * 2;
-    a.off_xs = (a.off_cnt + kThreads * npairs + 15) & ~15;
-    // staging area: what is left of ~72 KiB (three CTAs per SM), at least 4 KiB
-    const int xs_bytes = std::max(4096, kStageXcBytes - a.off_xs) & ~15;
+    a.off_cnt = a.off_list + kThreads * kLcCap * 2;
+    a.off_xs = (a.off_cnt + kThreads * npairs + kThreads + 15) & ~15;
+    // staging area: what is left of ~52 KiB (four CTAs per SM), at least 1 KiB
+    const int xs_bytes = std::max(1024, kStageXcBytes - a.off_xs) & ~15;
     smem = size_t(a.off_xs) + xs_bytes;
     a.xs_cap = int(xs_bytes / sizeof(T));
     static int configured_lc = -1;

@@ -323,3 +323,30 @@ def test_argument_errors(ring8):
                        ((x.data_ptr(), x.data_ptr() + 8 * len(B), 2, 1, 0), -1),   # ld < ncols
                        ((x.data_ptr(), x.data_ptr() + 8 * len(B), 1, 1, 7), -1)]:  # dtype
         assert ctx.L.mcd_apply(ctx.h, *args) == code
+
+
+def test_multi_column_list_overflow():
+    # complete bipartite K(8,8), uniform t (8 partner classes): the down word
+    # with all electrons on one side has 64 active bonds, every target in the
+    # basis (one up word with all C(16, 8) down words), more hops than a
+    # state's list in the multi-column kernel holds; they are found again
+    n = 16
+    t = np.zeros((n, n))
+    for i in range(8):
+        for j in range(8, 16):
+            t[i, j] = t[j, i] = -1.0
+    lat = L.Lattice("k88", n, t, np.zeros((n, 2), int), np.arange(n) // 8)
+    w = C.Workload("k88", lat, 2.0, 8, 8, 0, 0.2)
+    dns = np.array(fock.words_with_popcount(n, 8), dtype=np.uint64)
+    ups = fock.words_with_popcount(n, 8)
+    rng = np.random.default_rng(9)
+    B = np.unique(np.concatenate([(np.uint64(0x00FF) << np.uint64(n)) | dns] +
+                                 [(np.uint64(ups[k]) << np.uint64(n)) | dns[rng.choice(len(dns), 500, replace=False)]
+                                  for k in (5, 700, 9000)]))
+    ctx = device_ctx(w, basis=B)
+    P = H.build(model(w), B)
+    for algo in [(pkg.HV_AUTO, 1024), (pkg.HV_SEARCH, 1024)]:
+        with_algo(ctx, algo)
+        for dt in (np.float64, np.float32):
+            for nc in (2, 8, 24):
+                check_apply(ctx, P, t, nc, dt, seed=nc)
