@@ -168,3 +168,87 @@ def green(model: H.Model, basis: np.ndarray, psi: np.ndarray, E0: float, orbital
 def dos(G: np.ndarray) -> np.ndarray:
     """A(omega) = -(1/pi) Im sum_mu G_mu mu (Eq. DOS)."""
     return -np.imag(np.einsum("zaa->z", G)) / np.pi
+
+
+def parameters(model: H.Model):
+    """The Hamiltonian's parameters, in the order of the gradients: one per
+    bond (i < j, t_ij != 0), then eps_i and U_i of every site.  Each entry is
+    (kind, i, j) and unit(entry) is the model with that parameter alone = 1."""
+    n = model.n
+    out = [("t", i, j) for i in range(n) for j in range(i + 1, n) if model.t[i, j] != 0.0]
+    out += [("eps", i, i) for i in range(n)] + [("U", i, i) for i in range(n)]
+    return out
+
+
+def unit_model(n: int, par) -> H.Model:
+    kind, i, j = par
+    t, e, u = np.zeros((n, n)), np.zeros(n), np.zeros(n)
+    if kind == "t":
+        t[i, j] = t[j, i] = 1.0
+    elif kind == "eps":
+        e[i] = 1.0
+    else:
+        u[i] = 1.0
+    return H.Model(n, t, e, u)
+
+
+def green_gradient(model: H.Model, basis: np.ndarray, orbitals, w_t: float, z: np.ndarray,
+                   gR: np.ndarray, gI: np.ndarray):
+    """Gradient of S = sum_{z, mu, nu} gR Re G_{mu nu}(z) + gI Im G_{mu nu}(z)
+    with respect to (t_ij per bond, eps_i, U_i), for G computed with the exact
+    resolvent in the truncated excited subspaces (the limit the band Lanczos
+    reaches) and the set of kept ground-state words held fixed.
+
+    Plain dense definition, parameter by parameter (H is linear in them):
+      dE0 = <Omega| dH |Omega>                                   (Hellmann-Feynman)
+      dOmega = -(H - E0)^+ (dH - dE0) |Omega>                    (first-order perturbation)
+      Omega_t = P Omega / |P Omega|  =>  dOmega_t = (P dOmega - Omega_t <Omega_t|P dOmega>) / |P Omega|
+      phi_nu = c^dag_nu Omega_t (particle), c_nu Omega_t (hole), linear in Omega_t
+      G+ = phi^T (z + E0 - H+)^-1 phi,  G- = phi^T (z - E0 + H-)^-1 phi
+      dG = dphi^T R phi + phi^T R dphi - phi^T R dA R phi,  dA = +-(dE0) -+ dH+-.
+    Returns (grad_t [n, n] symmetric, 0 off the bonds, grad_eps [n], grad_U [n])."""
+    n = model.n
+    basis = np.asarray(basis, dtype=np.uint64)
+    Hd = H.build(model, basis).dense()
+    w, V = np.linalg.eigh(Hd)
+    E0, Om = float(w[0]), V[:, 0]
+    keep, coef = truncate(Om, w_t)
+    words = basis[keep]
+    Pn = float(np.linalg.norm(Om[keep]))
+    pinv = (V[:, 1:] / (w[1:] - E0)) @ V[:, 1:].T
+    z = np.asarray(z, dtype=np.complex128)
+    gc = np.asarray(gR, dtype=np.float64) + 1j * np.asarray(gI, dtype=np.float64)   # [nz, L, L]
+    sides = []
+    for dag in (True, False):
+        exc = excited_basis(words, n, orbitals, dag)
+        Phi = start_vectors(exc, words, coef, n, orbitals, dag)
+        Hs = H.build(model, exc).dense()
+        sgn = 1.0 if dag else -1.0
+        R = [np.linalg.inv((zz + sgn * E0) * np.eye(len(exc)) - sgn * Hs) for zz in z]
+        sides.append((dag, exc, Phi, sgn, R))
+    gt, ge, gu = np.zeros((n, n)), np.zeros(n), np.zeros(n)
+    for par in parameters(model):
+        um = unit_model(n, par)
+        dH = H.build(um, basis).dense()
+        dE0 = float(Om @ dH @ Om)
+        dOm = -pinv @ ((dH - dE0 * np.eye(len(basis))) @ Om)
+        dPt = dOm[keep]
+        dcoef = (dPt - coef * float(coef @ dPt)) / Pn
+        total = 0.0
+        for dag, exc, Phi, sgn, R in sides:
+            dPhi = start_vectors(exc, words, dcoef, n, orbitals, dag)
+            dHs = H.build(um, exc).dense()
+            dA = sgn * dE0 * np.eye(len(exc)) - sgn * dHs
+            for iz in range(len(z)):
+                Rz = R[iz]
+                RPhi = Rz @ Phi
+                dG = dPhi.T @ RPhi + RPhi.T @ dPhi - RPhi.T @ dA @ RPhi
+                total += float(np.sum(np.real(np.conj(gc[iz]) * dG)))
+        kind, i, j = par
+        if kind == "t":
+            gt[i, j] = gt[j, i] = total
+        elif kind == "eps":
+            ge[i] = total
+        else:
+            gu[i] = total
+    return gt, ge, gu
