@@ -217,6 +217,27 @@ int mcd_band_lanczos_green(mcd_ctx* ctx, const int* orb_site, const int* orb_spi
                            const double* z_im, int nz, double* G_re, double* G_im,
                            int64_t* dim_plus, int64_t* dim_minus);
 
+/* Gradient of the Green function with respect to the Hamiltonian's
+ * parameters (for fitting bath parameters to a target G(i omega_n)), as a
+ * vector-Jacobian product: the gradient of
+ *   S = sum_{z, mu, nu} gG_re[z][mu][nu] Re G_mu nu(z) + gG_im[z][mu][nu] Im G_mu nu(z)
+ * with G as mcd_band_lanczos_green computes it (same orbitals, n_block_iter,
+ * w_t, z; fp64 Krylov vectors) and the set of kept ground-state words held
+ * fixed.  Ingredients: Hellmann-Feynman dE0 = <Omega|dH|Omega>; the
+ * first-order ground-state response (H - E0) dOmega = -(dH - dE0) Omega,
+ * solved once for the contracted right-hand side by conjugate gradients
+ * (relative residual cg_tol, e.g. 1e-11); the resolvent's derivative in each
+ * excited space from the band run's Ritz vectors (all Krylov blocks are kept:
+ * |F~+-| x n_block_iter x L doubles each, MCD_E_OOM if they do not fit).
+ * grad_t: host [n][n] (bond derivative at [i][j] and [j][i], 0 off the
+ * bonds); grad_eps, grad_U: host [n].  *cg_iters (nullable): CG iterations.
+ * MCD_E_STATE without a ground state; MCD_E_NOT_CONVERGED if CG does not reach
+ * cg_tol (gradients still filled). */
+int mcd_green_gradient(mcd_ctx* ctx, const int* orb_site, const int* orb_spin, int L, int n_block_iter,
+                       double w_t, const double* z_re, const double* z_im, int nz, const double* gG_re,
+                       const double* gG_im, double cg_tol, double* grad_t, double* grad_eps, double* grad_U,
+                       int* cg_iters);
+
 /* App. B/C (diagonalising the effective matrices): eigenvalues w[n]
  * (ascending) of the symmetric host matrix A[n][n] (row-major; not modified)
  * and the first `rows` rows of its eigenvector matrix X[rows][n] (column m =

@@ -60,6 +60,9 @@ _SIGS = {
                                               ctypes.c_int, c_dp, c_dp, c_i64p, c_i64p]),
     "mcd_symeig": (ctypes.c_int, [ctypes.c_int, c_dp, c_dp, ctypes.c_int, c_dp]),
     "mcd_hv_adjoint": (ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_dp, c_dp, c_dp]),
+    "mcd_green_gradient": (ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_double, c_dp, c_dp, ctypes.c_int, c_dp,
+                                          c_dp, ctypes.c_double, c_dp, c_dp, c_dp, ctypes.POINTER(ctypes.c_int)]),
     "mcd_batch_apply": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, c_vp, c_vp, ctypes.c_int]),
     "mcd_batch_lanczos_ground": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                 ctypes.c_uint64, ctypes.c_int, c_dp, ctypes.POINTER(ctypes.c_int),
@@ -328,6 +331,29 @@ class Context:
                                                   gr.ctypes.data_as(c_dp), gi.ctypes.data_as(c_dp),
                                                   ctypes.byref(dp), ctypes.byref(dm)))
         return gr + 1j * gi, dp.value, dm.value
+
+    def mcd_green_gradient(self, orbitals, n_block_iter: int, w_t: float, z, gG, cg_tol: float = 1e-11,
+                           allow_not_converged: bool = False):
+        """Gradient of sum Re(conj(gG) G) = sum gG.re Re G + gG.im Im G with respect
+        to (t [n, n], eps [n], U [n]); gG: complex [nz, L, L].  Returns
+        (grad_t, grad_eps, grad_U, cg_iters)."""
+        L = len(orbitals)
+        site = (ctypes.c_int * L)(*[int(o[0]) for o in orbitals])
+        spin = (ctypes.c_int * L)(*[int(o[1]) for o in orbitals])
+        z = np.ascontiguousarray(np.atleast_1d(z), dtype=np.complex128)
+        zr, zi = np.ascontiguousarray(z.real), np.ascontiguousarray(z.imag)
+        gG = np.asarray(gG, dtype=np.complex128).reshape(len(z), L, L)
+        gr, gi = np.ascontiguousarray(gG.real), np.ascontiguousarray(gG.imag)
+        n = self.n_sites
+        gt, ge, gu = np.zeros((n, n)), np.zeros(n), np.zeros(n)
+        it = ctypes.c_int(0)
+        self._sync_stream()
+        st = self.L.mcd_green_gradient(self.h, site, spin, L, n_block_iter, w_t, zr.ctypes.data_as(c_dp),
+                                       zi.ctypes.data_as(c_dp), len(z), gr.ctypes.data_as(c_dp),
+                                       gi.ctypes.data_as(c_dp), cg_tol, gt.ctypes.data_as(c_dp),
+                                       ge.ctypes.data_as(c_dp), gu.ctypes.data_as(c_dp), ctypes.byref(it))
+        self._check(st, ok=(MCD_OK, MCD_E_NOT_CONVERGED) if allow_not_converged else (MCD_OK,))
+        return gt, ge, gu, it.value
 
     def mcd_kernel_times(self, reset: bool = False):
         ms = (ctypes.c_double * 4)()

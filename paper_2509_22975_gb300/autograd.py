@@ -7,6 +7,9 @@ library's kernels).
 * ``ground_energy(ctx, t, eps, U, ...)``: Lanczos E0, differentiable in the
   parameters by Hellmann-Feynman, dE0/dtheta = <Omega~| dH/dtheta |Omega~>,
   evaluated by the same adjoint kernel with u = v = |Omega~>.
+* ``green(ctx, t, eps, U, orbitals, n_blocks, w_t, z)``: the band-Lanczos G(z)
+  as [nz, L, L, 2] (real, imaginary), differentiable in the parameters
+  (backward: ``mcd_green_gradient``).
 
 t is the full symmetric [n, n] hopping matrix; its gradient is returned
 symmetric with the bond derivative at [i, j] and [j, i] (0 where t_ij = 0).
@@ -88,4 +91,34 @@ def ground_energy(ctx, t, eps, U, max_iter: int = 400, tol: float = 1e-12, seed:
     return _E0.apply(ctx, t, eps, U, max_iter, tol, seed, dtype)
 
 
-__all__ = ["hv", "ground_energy", "MCD_F32", "MCD_F64"]
+class _Green(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, ctx, t, eps, U, orbitals, n_blocks, w_t, z, max_iter, tol):
+        _set(ctx, t, eps, U)
+        n = ctx.mcd_basis_info(nnz=False)["n_states"]
+        psi = torch.empty(n, dtype=torch.float64, device=torch.device("cuda", ctx.device))
+        ctx.mcd_lanczos_ground(max_iter, tol, 0, MCD_F64, psi=psi, allow_not_converged=True)
+        G, _, _ = ctx.mcd_band_lanczos_green(orbitals, n_blocks, w_t, z)
+        fctx.ctx = ctx
+        fctx.args = (orbitals, n_blocks, w_t, z)
+        fctx.save_for_backward(t, eps, U)
+        return torch.stack([torch.from_numpy(G.real), torch.from_numpy(G.imag)], dim=-1)
+
+    @staticmethod
+    def backward(fctx, gG):
+        t, eps, U = fctx.saved_tensors
+        orbitals, n_blocks, w_t, z = fctx.args
+        g = gG.detach().cpu().double().numpy()
+        gt, ge, gu, _ = fctx.ctx.mcd_green_gradient(orbitals, n_blocks, w_t, z, g[..., 0] + 1j * g[..., 1])
+        return None, _like(gt, t), _like(ge, eps), _grad_U(gu, U), None, None, None, None, None, None
+
+
+def green(ctx, t, eps, U, orbitals, n_blocks: int, w_t: float, z, max_iter: int = 800, tol: float = 1e-13):
+    """G(z) of H~(t, eps, U) on the context's basis (band Lanczos, fp64), as a real
+    tensor [nz, L, L, 2] (real and imaginary parts); differentiable in the
+    parameters through mcd_green_gradient."""
+    z = np.ascontiguousarray(np.atleast_1d(z), dtype=np.complex128)
+    return _Green.apply(ctx, t, eps, U, list(orbitals), n_blocks, w_t, z, max_iter, tol)
+
+
+__all__ = ["hv", "ground_energy", "green", "MCD_F32", "MCD_F64"]

@@ -19,6 +19,7 @@
 //    sums of the Q-matrix Eqs. summed over the particle and hole runs.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <vector>
 
@@ -208,9 +209,21 @@ void factors(int p, int r, const std::vector<int>& piv, const std::vector<double
 struct BandRun {
   std::vector<double> E;   // eigenvalues of H_eff
   std::vector<double> Q;   // [L][K]
+  std::vector<double> S;   // [K][K] eigenvectors of H_eff (only when the blocks are kept)
   int64_t dim = 0;
   int K = 0;
 };
+
+// dst[r][off + j] = src[r][j] (j < p): one Krylov block into the kept [n][kmax] array
+template <typename T>
+__global__ void keep_block_kernel(const T* src, int ld_src, int p, double* dst, int kmax, int off, int64_t n) {
+  const int64_t total = n * p;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e / p;
+    const int j = int(e - r * p);
+    dst[r * kmax + off + j] = double(src[r * ld_src + j]);
+  }
+}
 
 template <typename T>
 class BandLanczos {
@@ -233,6 +246,11 @@ class BandLanczos {
     return MCD_OK;
   }
   T* buf(int i) { return B_[i]; }
+  // keep every Krylov block in vall[n][kmax] (fp64) and return all eigenvectors
+  void keep_blocks(double* vall, int kmax) {
+    vall_ = vall;
+    kmax_ = kmax;
+  }
 
   // host G = X[:, :pa]^T Y[:, :pb]
   int gram(const T* X, int pa, const T* Y, int pb, std::vector<double>& G) {
@@ -320,8 +338,15 @@ class BandLanczos {
     std::vector<int> ps;
     int pprev = 0;
     std::vector<double> Bprev;   // B_k: p_k x p_{k-1}
+    int kept = 0;
     for (int k = 0; k < n_blocks && p > 0; ++k) {
       ps.push_back(p);
+      if (vall_) {
+        if (kept + p > kmax_) return fail(c_, MCD_E_INVALID, "band Lanczos: kept blocks exceed their storage");
+        keep_block_kernel<T><<<grid_for(n_ * p), kThreads, 0, c_->stream>>>(Vcur, L_, p, vall_, kmax_, kept, n_);
+        MCD_LAUNCHED(c_);
+        kept += p;
+      }
       st = hv_apply(c_, Vcur, W, p, L_, sizeof(T) == 8 ? MCD_F64 : MCD_F32, nullptr, 0);
       if (st) return st;
       std::vector<double> Gw;
@@ -394,9 +419,11 @@ class BandLanczos {
       }
     }
     out.E.assign(K, 0.0);
-    std::vector<double> X(size_t(p1) * K, 0.0);
-    if (symeig_leading(K, Hm.data(), out.E.data(), p1, X.data()) != 0)
+    const int rows = vall_ ? K : p1;
+    std::vector<double> X(size_t(rows) * K, 0.0);
+    if (symeig_leading(K, Hm.data(), out.E.data(), rows, X.data()) != 0)
       return fail(c_, MCD_E_NOT_CONVERGED, "band Lanczos: H_eff eigensolver did not converge");
+    if (vall_) out.S = X;
     // Q[mu][m] = sum_{i < p1} R0[i][mu] X[i][m]
     out.Q.assign(size_t(L_) * K, 0.0);
     for (int mu = 0; mu < L_; ++mu)
@@ -419,11 +446,209 @@ class BandLanczos {
   double* gram_ = nullptr;
   double* coef_ = nullptr;
   int nparts_ = 1;
+  double* vall_ = nullptr;
+  int kmax_ = 0;
 };
+
+// ---- gradient of G with respect to the Hamiltonian's parameters -----------------
+
+// out[r][j] = sum_i A[r][i] M[i][j]  (A: n x k, M: k x cols, fp64, row-major)
+__global__ void gemm_rows_kernel(const double* __restrict__ A, int64_t n, int k, const double* __restrict__ M,
+                                 int cols, double* out) {
+  const int64_t total = n * cols;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e / cols;
+    const int j = int(e - r * cols);
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s = fma(A[r * k + i], __ldg(M + int64_t(i) * cols + j), s);
+    out[e] = s;
+  }
+}
+
+// r[i] += sum_nu <x| c^(dag)_nu |w_i> F[x][nu]: the start-vector map (start_vec_kernel)
+// transposed, one thread per kept ground-state word (deterministic)
+__global__ void map_back_kernel(const uint64_t* __restrict__ gw, int64_t ng, const uint64_t* __restrict__ exc,
+                                int64_t ne, const double* __restrict__ F, const OrbParams op, double* r) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= ng) return;
+  const uint64_t w = gw[i];
+  const int n = op.n_sites;
+  const uint64_t half = n == 32 ? 0xFFFFFFFFull : ((1ull << n) - 1);
+  double acc = 0.0;
+  for (int nu = 0; nu < op.L; ++nu) {
+    const int sh = op.spin[nu] == 0 ? n + op.site[nu] : op.site[nu];
+    const uint64_t bit = 1ull << sh;
+    const bool occ = (w & bit) != 0;
+    if (occ == bool(op.dagger)) continue;
+    const uint64_t x = w ^ bit;
+    int64_t lo = 0, len = ne;
+    while (len > 1) {
+      const int64_t h = len >> 1;
+      if (exc[lo + h] <= x) lo += h;
+      len -= h;
+    }
+    if (ne == 0 || exc[lo] != x) continue;
+    const uint32_t up = uint32_t(w >> n), dn = uint32_t(w & half);
+    const int st = op.site[nu];
+    const uint32_t below = (st == 0) ? 0u : (0xFFFFFFFFu >> (32 - st));
+    const int before = op.spin[nu] == 0 ? __popc(up & below) : __popc(up) + __popc(dn & below);
+    const double f = F[lo * op.L + nu];
+    acc += (before & 1) ? -f : f;
+  }
+  r[i] += acc;
+}
+
+// y = a x + b y
+__global__ void axpby_kernel(double a, const double* x, double b, double* y, int64_t n) {
+  for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+    y[k] = a * x[k] + b * y[k];
+}
+
+// per-block partial sums of a[k] b[k] (summed on the host in block order)
+__global__ void __launch_bounds__(kThreads) dot_part_kernel(const double* a, const double* b, int64_t n, double* part) {
+  __shared__ double s_red[kThreads / 32];
+  double acc = 0.0;
+  for (int64_t k = int64_t(blockIdx.x) * kThreads + threadIdx.x; k < n; k += int64_t(gridDim.x) * kThreads)
+    acc = fma(a[k], b[k], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) t += s_red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// What the gradient takes from one excited space and what it gives back.
+struct GradSide {
+  const double* z_re;
+  const double* z_im;
+  int nz;
+  const double* g_re;      // [nz][L][L] upstream gradient of Re G
+  const double* g_im;      //            and of Im G
+  double E0;
+  double* d_r;             // device [n kept]: start-vector term, accumulated
+  std::vector<double> gt, ge, gu;   // resolvent term, accumulated
+  double cE = 0.0;                  // coefficient of dE0, accumulated
+};
+
+// The resolvent and start-vector terms of one excited space (sgn = +1
+// particle: A = z + E0 - H+; -1 hole: A = z - E0 + H-).  With y_m = V S_m the
+// Ritz vectors, beta_mu m(z) = Q_mu m / (z + sgn E0 - sgn E_m) and
+// b_mu(z) = sum_m beta_mu m y_m = A^-1 phi_mu on the Krylov space:
+//   dG_mu nu = dphi_mu^T b_nu + b_mu^T dphi_nu + sgn b_mu^T dH b_nu - sgn dE0 b_mu^T b_nu.
+// Contracted with conj(g): Gamma_mm' = Re sum conj(g_mu nu) beta_mu m beta_nu m'
+// gives sgn sum Gamma_mm' y_m^T dH y_m' (one adjoint call, U = V S, V2 = V S
+// (sgn Gamma)^T), the dE0 coefficient -sgn tr Gamma, and the vectors
+// f_mu = sum_m y_m Re sum (conj(g_mu nu) + conj(g_nu mu)) beta_nu m mapped
+// back onto the kept ground-state words by the transposed start-vector map.
+int grad_side(mcd_ctx* c, mcd_ctx* sub, const double* vall, int64_t N, const BandRun& run, int L, bool dagger,
+              const uint64_t* dgw, int64_t ng, const OrbParams& op, GradSide& gs) {
+  const int K = run.K;
+  if (K == 0) return MCD_OK;
+  const double sgn = dagger ? 1.0 : -1.0;
+  const int nz = gs.nz;
+  std::vector<double> Gam(size_t(K) * K, 0.0), A(size_t(L) * K, 0.0);
+  std::vector<std::complex<double>> beta(size_t(L) * K), Cm(size_t(L) * K);
+  for (int iz = 0; iz < nz; ++iz) {
+    const std::complex<double> z(gs.z_re[iz], gs.z_im[iz]);
+    for (int m = 0; m < K; ++m) {
+      const std::complex<double> inv = 1.0 / (z + sgn * gs.E0 - sgn * run.E[m]);
+      for (int mu = 0; mu < L; ++mu) beta[size_t(mu) * K + m] = run.Q[size_t(mu) * K + m] * inv;
+    }
+    const double* gr = gs.g_re + size_t(iz) * L * L;
+    const double* gi = gs.g_im + size_t(iz) * L * L;
+    // Cm[nu][m] = sum_mu conj(g_mu nu) beta_mu m ; A[mu][m] += Re sum_nu (conj g_mu nu + conj g_nu mu) beta_nu m
+    for (int nu = 0; nu < L; ++nu)
+      for (int m = 0; m < K; ++m) {
+        std::complex<double> acc = 0.0;
+        for (int mu = 0; mu < L; ++mu)
+          acc += std::complex<double>(gr[mu * L + nu], -gi[mu * L + nu]) * beta[size_t(mu) * K + m];
+        Cm[size_t(nu) * K + m] = acc;
+      }
+    for (int mu = 0; mu < L; ++mu)
+      for (int m = 0; m < K; ++m) {
+        std::complex<double> acc = 0.0;
+        for (int nu = 0; nu < L; ++nu) {
+          const std::complex<double> g1(gr[mu * L + nu], -gi[mu * L + nu]), g2(gr[nu * L + mu], -gi[nu * L + mu]);
+          acc += (g1 + g2) * beta[size_t(nu) * K + m];
+        }
+        A[size_t(mu) * K + m] += acc.real();
+      }
+    for (int m = 0; m < K; ++m)
+      for (int mp = 0; mp < K; ++mp) {
+        std::complex<double> acc = 0.0;
+        for (int nu = 0; nu < L; ++nu) acc += Cm[size_t(nu) * K + m] * beta[size_t(nu) * K + mp];
+        Gam[size_t(m) * K + mp] += acc.real();
+      }
+  }
+  for (int m = 0; m < K; ++m) gs.cE += -sgn * Gam[size_t(m) * K + m];
+  // M1 = S, M2 = S (sgn Gamma)^T, M3 = S A^T (host, K x K and K x L)
+  const std::vector<double>& S = run.S;
+  std::vector<double> M2(size_t(K) * K, 0.0), M3(size_t(K) * L, 0.0);
+  for (int k = 0; k < K; ++k)
+    for (int m = 0; m < K; ++m) {
+      const double skm = S[size_t(k) * K + m];
+      if (skm == 0.0) continue;
+      for (int j = 0; j < K; ++j) M2[size_t(k) * K + j] += skm * sgn * Gam[size_t(j) * K + m];
+      for (int mu = 0; mu < L; ++mu) M3[size_t(k) * L + mu] += skm * A[size_t(mu) * K + m];
+    }
+  cudaStream_t s = c->stream;
+  double *dM = nullptr, *U = nullptr, *V2 = nullptr, *F = nullptr;
+  cudaError_t e = cudaMalloc(&dM, sizeof(double) * (size_t(K) * K * 2 + size_t(K) * L));
+  if (e == cudaSuccess) e = cudaMalloc(&U, sizeof(double) * size_t(N) * K);
+  if (e == cudaSuccess) e = cudaMalloc(&V2, sizeof(double) * size_t(N) * K);
+  if (e == cudaSuccess) e = cudaMalloc(&F, sizeof(double) * size_t(N) * L);
+  auto release = [&]() {
+    for (double* q : {dM, U, V2, F})
+      if (q) cudaFree(q);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return fail(c, MCD_E_OOM, "Green gradient: Ritz-vector buffers");
+  }
+  e = cudaMemcpyAsync(dM, S.data(), sizeof(double) * K * K, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dM + size_t(K) * K, M2.data(), sizeof(double) * K * K, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dM + 2 * size_t(K) * K, M3.data(), sizeof(double) * K * L, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    gemm_rows_kernel<<<grid_for(N * K), kThreads, 0, s>>>(vall, N, K, dM, K, U);
+    gemm_rows_kernel<<<grid_for(N * K), kThreads, 0, s>>>(vall, N, K, dM + size_t(K) * K, K, V2);
+    gemm_rows_kernel<<<grid_for(N * L), kThreads, 0, s>>>(vall, N, K, dM + 2 * size_t(K) * K, L, F);
+    c->launches += 3;
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "Green gradient: Ritz vectors");
+  }
+  const int n = c->n;
+  std::vector<double> gt(size_t(n) * n), ge(n), gu(n);
+  const int64_t before = sub->launches;
+  int st = hv_adjoint(sub, U, V2, K, K, MCD_F64, gt.data(), ge.data(), gu.data());
+  c->launches += sub->launches - before;
+  if (st != MCD_OK) {
+    release();
+    return fail(c, st, std::string("Green gradient: adjoint: ") + sub->err);
+  }
+  for (size_t i = 0; i < gt.size(); ++i) gs.gt[i] += gt[i];
+  for (int i = 0; i < n; ++i) {
+    gs.ge[i] += ge[i];
+    gs.gu[i] += gu[i];
+  }
+  map_back_kernel<<<int((ng + 255) / 256), 256, 0, s>>>(dgw, ng, sub->idx.words, N, F, op, gs.d_r);
+  MCD_LAUNCHED(c);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  return e == cudaSuccess ? MCD_OK : cuda_fail(c, e, "Green gradient: start-vector term");
+}
 
 template <typename T>
 int one_side(mcd_ctx* c, const std::vector<uint64_t>& kept_w, const std::vector<double>& kept_c, const int* site,
-             const int* spin, int L, bool dagger, int n_blocks, BandRun& out) {
+             const int* spin, int L, bool dagger, int n_blocks, BandRun& out, GradSide* gs = nullptr) {
   const int n = c->n;
   const int sp = spin[0];
   // excited basis (host): c^dag_mu w or c_mu w over kept w
@@ -473,9 +698,19 @@ int one_side(mcd_ctx* c, const std::vector<uint64_t>& kept_w, const std::vector<
   }
   BandLanczos<T> bl(sub, L);
   st = bl.alloc();
+  double* vall = nullptr;
+  const int kmax = n_blocks * L;
+  if (st == MCD_OK && gs) {
+    if (cudaMalloc(&vall, sizeof(double) * size_t(exc.size()) * kmax) != cudaSuccess) {
+      vall = nullptr;
+      st = fail(c, MCD_E_OOM, "Green gradient: the Krylov blocks of an excited space do not fit");
+    } else {
+      bl.keep_blocks(vall, kmax);
+    }
+  }
+  OrbParams op;
+  std::memset(&op, 0, sizeof(op));
   if (st == MCD_OK) {
-    OrbParams op;
-    std::memset(&op, 0, sizeof(op));
     op.L = L;
     op.dagger = dagger ? 1 : 0;
     op.n_sites = n;
@@ -495,16 +730,19 @@ int one_side(mcd_ctx* c, const std::vector<uint64_t>& kept_w, const std::vector<
     if (st != MCD_OK) c->err = sub->err;
   }
   c->launches += sub->launches - before;
+  if (st == MCD_OK && gs) {
+    const int64_t b2 = sub->launches;
+    st = grad_side(c, sub, vall, int64_t(exc.size()), out, L, dagger, dgw, int64_t(kept_w.size()), op, *gs);
+    c->launches += sub->launches - b2;
+  }
+  if (vall) cudaFree(vall);
   cudaFree(dgw);
   cudaFree(dgc);
   return st;
 }
 
-}  // namespace
-
-int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int n_blocks, double w_t, int dtype,
-                       const double* z_re, const double* z_im, int nz, double* G_re, double* G_im,
-                       int64_t* dim_plus, int64_t* dim_minus) {
+// argument checks shared by the Green function and its gradient
+int check_orbitals(mcd_ctx* c, const int* site, const int* spin, int L, int n_blocks, double w_t) {
   if (!c->gs_valid) return fail(c, MCD_E_STATE, "no ground state: call mcd_lanczos_ground first");
   if (L < 1 || L > kMaxOrb) return fail(c, MCD_E_INVALID, "need 1 <= L <= 64 orbitals");
   for (int mu = 0; mu < L; ++mu) {
@@ -515,10 +753,17 @@ int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int 
   }
   if (n_blocks < 1) return fail(c, MCD_E_INVALID, "n_block_iter must be >= 1");
   if (!(w_t > 0.0 && w_t <= 1.0)) return fail(c, MCD_E_INVALID, "w_t must be in (0, 1]");
+  return MCD_OK;
+}
+
+// Target-weight truncation (Sec. "Further truncation"): largest |c|^2 first,
+// ties by basis index, shortest prefix reaching w_t of the norm.  psi = the
+// normalised ground state (host), keep = kept basis indices (ascending), kw/kc
+// = their words and renormalised coefficients, kn = |P psi|^2.
+int kept_ground_state(mcd_ctx* c, double w_t, std::vector<double>& psi, std::vector<int64_t>& keep,
+                      std::vector<uint64_t>& kw, std::vector<double>& kc, double& kn) {
   const int64_t N = c->idx.n;
-  // target-weight truncation (Sec. "Further truncation"): largest |c|^2 first,
-  // ties by basis index, shortest prefix reaching w_t of the norm
-  std::vector<double> psi(N);
+  psi.resize(N);
   cudaError_t e = cudaMemcpyAsync(psi.data(), c->gs_psi, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "copy ground state");
@@ -539,11 +784,11 @@ int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int 
   const double target = w_t * cum[N - 1] * (1.0 - 1e-15);
   int64_t k = int64_t(std::lower_bound(cum.begin(), cum.end(), target) - cum.begin()) + 1;
   if (k > N) k = N;
-  std::vector<int64_t> keep(order.begin(), order.begin() + k);
+  keep.assign(order.begin(), order.begin() + k);
   std::sort(keep.begin(), keep.end());
-  std::vector<uint64_t> kw(k);
-  std::vector<double> kc(k);
-  double kn = 0.0;
+  kw.resize(k);
+  kc.resize(k);
+  kn = 0.0;
   for (int64_t i = 0; i < k; ++i) {
     kw[i] = c->basis_on_host ? c->basis[keep[i]] : 0;
     kc[i] = psi[keep[i]];
@@ -556,6 +801,25 @@ int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int 
     for (int64_t i = 0; i < k; ++i) kw[i] = all[keep[i]];
   }
   for (double& v : kc) v /= std::sqrt(kn);
+  // psi and kn for a normalised psi
+  for (double& v : psi) v *= inv;
+  kn *= inv * inv;
+  return MCD_OK;
+}
+
+}  // namespace
+
+int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int n_blocks, double w_t, int dtype,
+                       const double* z_re, const double* z_im, int nz, double* G_re, double* G_im,
+                       int64_t* dim_plus, int64_t* dim_minus) {
+  int st0 = check_orbitals(c, site, spin, L, n_blocks, w_t);
+  if (st0 != MCD_OK) return st0;
+  std::vector<double> psi, kc;
+  std::vector<int64_t> keep;
+  std::vector<uint64_t> kw;
+  double kn = 0.0;
+  st0 = kept_ground_state(c, w_t, psi, keep, kw, kc, kn);
+  if (st0 != MCD_OK) return st0;
   BandRun plus, minus;
   int st = dtype == MCD_F64 ? one_side<double>(c, kw, kc, site, spin, L, true, n_blocks, plus)
                             : one_side<float>(c, kw, kc, site, spin, L, true, n_blocks, plus);
@@ -587,6 +851,140 @@ int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int 
         G_im[(size_t(iz) * L + a) * L + b] = im;
       }
   }
+  return MCD_OK;
+}
+
+// Gradient of S = sum_{z,mu,nu} gR Re G_mu nu(z) + gI Im G_mu nu(z) with respect
+// to (t_ij per bond, eps_i, U_i), G as mcd_band_lanczos_green computes it (the
+// Krylov resolvent in the truncated excited spaces), the kept ground-state
+// words held fixed.  Besides the two excited-space terms (grad_side):
+//   dE0 = <Omega|dH|Omega> (Hellmann-Feynman) with the accumulated coefficient;
+//   the start vectors phi = c^(dag) P Omega / |P Omega| depend on Omega: the
+//   map-back r (on the kept words) becomes, through the renormalisation,
+//   rt = P (r - Omega_t <Omega_t|r>) / |P Omega|, and with the first-order
+//   response dOmega = -(H - E0)^+ (dH - dE0) Omega the term is -lambda^T dH Omega,
+//   lambda = (H - E0)^+ rt_perp, found by conjugate gradients on the
+//   complement of Omega.  One last adjoint call takes u = cE Omega - lambda.
+int green_gradient(mcd_ctx* c, const int* site, const int* spin, int L, int n_blocks, double w_t,
+                   const double* z_re, const double* z_im, int nz, const double* g_re, const double* g_im,
+                   double* grad_t, double* grad_eps, double* grad_U, double cg_tol, int* cg_iters) {
+  int st = check_orbitals(c, site, spin, L, n_blocks, w_t);
+  if (st != MCD_OK) return st;
+  std::vector<double> psi, kc;
+  std::vector<int64_t> keep;
+  std::vector<uint64_t> kw;
+  double kn = 0.0;
+  st = kept_ground_state(c, w_t, psi, keep, kw, kc, kn);
+  if (st != MCD_OK) return st;
+  const int n = c->n;
+  const int64_t N = c->idx.n, nk = int64_t(keep.size());
+  cudaStream_t s = c->stream;
+  GradSide gs;
+  gs.z_re = z_re;
+  gs.z_im = z_im;
+  gs.nz = nz;
+  gs.g_re = g_re;
+  gs.g_im = g_im;
+  gs.E0 = c->gs_E0;
+  gs.gt.assign(size_t(n) * n, 0.0);
+  gs.ge.assign(n, 0.0);
+  gs.gu.assign(n, 0.0);
+  double* buf = nullptr;   // d_r [nk] | b, lam, r, p, q, u [N each] | partials [kParts]
+  constexpr int kParts = 152 * 4;
+  cudaError_t e = cudaMalloc(&buf, sizeof(double) * (size_t(nk) + 6 * size_t(N) + kParts));
+  if (e != cudaSuccess) return fail(c, MCD_E_OOM, "Green gradient: work vectors");
+  struct Free {
+    double* p;
+    ~Free() { cudaFree(p); }
+  } guard{buf};
+  gs.d_r = buf;
+  double* vb = buf + nk;
+  double* lam = vb + N;
+  double* r = lam + N;
+  double* pv = r + N;
+  double* q = pv + N;
+  double* u = q + N;
+  double* part = u + N;
+  e = cudaMemsetAsync(buf, 0, sizeof(double) * (size_t(nk) + 6 * size_t(N)), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "Green gradient: clear");
+  BandRun plus, minus;
+  st = one_side<double>(c, kw, kc, site, spin, L, true, n_blocks, plus, &gs);
+  if (st == MCD_OK) st = one_side<double>(c, kw, kc, site, spin, L, false, n_blocks, minus, &gs);
+  if (st != MCD_OK) return st;
+  // start-vector term through the renormalised truncation, on the full basis
+  std::vector<double> rk(nk), b(N, 0.0);
+  e = cudaMemcpyAsync(rk.data(), gs.d_r, sizeof(double) * nk, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "Green gradient: start-vector term");
+  double kr = 0.0;
+  for (int64_t i = 0; i < nk; ++i) kr += kc[i] * rk[i];
+  const double pn = std::sqrt(kn);
+  for (int64_t i = 0; i < nk; ++i) b[keep[i]] = (rk[i] - kc[i] * kr) / pn;
+  double ob = 0.0;
+  for (int64_t i = 0; i < N; ++i) ob += psi[i] * b[i];
+  for (int64_t i = 0; i < N; ++i) b[i] -= ob * psi[i];
+  e = cudaMemcpyAsync(vb, b.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "Green gradient: right-hand side");
+  const double* om = c->gs_psi;
+  const int vg = grid_for(N);
+  auto dot = [&](const double* x, const double* y, double& out) -> int {
+    dot_part_kernel<<<kParts, kThreads, 0, s>>>(x, y, N, part);
+    MCD_LAUNCHED(c);
+    std::vector<double> h(kParts);
+    cudaError_t er = cudaMemcpyAsync(h.data(), part, sizeof(double) * kParts, cudaMemcpyDeviceToHost, s);
+    if (er == cudaSuccess) er = cudaStreamSynchronize(s);
+    if (er != cudaSuccess) return cuda_fail(c, er, "Green gradient: dot");
+    out = 0.0;
+    for (double v : h) out += v;
+    return MCD_OK;
+  };
+  auto axpby = [&](double a, const double* x, double bb, double* y) {
+    axpby_kernel<<<vg, kThreads, 0, s>>>(a, x, bb, y, N);
+    MCD_LAUNCHED(c);
+  };
+  // conjugate gradients for (H - E0) lam = b on the complement of Omega
+  const double E0 = c->gs_E0;
+  double rr = 0.0;
+  e = cudaMemcpyAsync(r, vb, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pv, vb, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "Green gradient: CG start");
+  if ((st = dot(r, r, rr)) != MCD_OK) return st;
+  const double bnorm = std::sqrt(rr);
+  int it = 0;
+  bool conv = bnorm == 0.0;
+  const int max_it = 20000;
+  for (; !conv && it < max_it; ++it) {
+    st = hv_apply(c, pv, q, 1, 1, MCD_F64, nullptr, 0);
+    if (st != MCD_OK) return st;
+    axpby(-E0, pv, 1.0, q);
+    double oq = 0.0, pq = 0.0, rn = 0.0, orr = 0.0;
+    if ((st = dot(om, q, oq)) != MCD_OK) return st;
+    axpby(-oq, om, 1.0, q);
+    if ((st = dot(pv, q, pq)) != MCD_OK) return st;
+    if (!(pq > 0.0)) return fail(c, MCD_E_BREAKDOWN, "Green gradient: H - E0 not positive on the complement");
+    const double alpha = rr / pq;
+    axpby(alpha, pv, 1.0, lam);
+    axpby(-alpha, q, 1.0, r);
+    if ((st = dot(om, r, orr)) != MCD_OK) return st;
+    axpby(-orr, om, 1.0, r);
+    if ((st = dot(r, r, rn)) != MCD_OK) return st;
+    if (std::sqrt(rn) <= cg_tol * bnorm) conv = true;
+    axpby(1.0, r, rn / rr, pv);
+    rr = rn;
+  }
+  if (cg_iters) *cg_iters = it;
+  // last adjoint: u = cE Omega - lam against Omega
+  axpby(gs.cE, om, 0.0, u);
+  axpby(-1.0, lam, 1.0, u);
+  std::vector<double> gt(size_t(n) * n), ge(n), gu(n);
+  st = hv_adjoint(c, u, om, 1, 1, MCD_F64, gt.data(), ge.data(), gu.data());
+  if (st != MCD_OK) return st;
+  for (int i = 0; i < n * n; ++i) grad_t[i] = gs.gt[i] + gt[i];
+  for (int i = 0; i < n; ++i) {
+    grad_eps[i] = gs.ge[i] + ge[i];
+    grad_U[i] = gs.gu[i] + gu[i];
+  }
+  if (!conv) return fail(c, MCD_E_NOT_CONVERGED, "Green gradient: conjugate gradients did not converge");
   return MCD_OK;
 }
 

@@ -598,6 +598,24 @@ int mcd_band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, 
   }
 }
 
+int mcd_green_gradient(mcd_ctx* c, const int* site, const int* spin, int L, int n_block_iter, double w_t,
+                       const double* z_re, const double* z_im, int nz, const double* g_re, const double* g_im,
+                       double cg_tol, double* grad_t, double* grad_eps, double* grad_U, int* cg_iters) {
+  if (!c) return MCD_E_INVALID;
+  int st = need_basis(c);
+  if (st != MCD_OK) return st;
+  if ((st = need_device(c)) != MCD_OK) return st;
+  if (!site || !spin || nz < 1 || !z_re || !z_im || !g_re || !g_im || !grad_t || !grad_eps || !grad_U)
+    return fail(c, MCD_E_INVALID, "null argument");
+  if (!(cg_tol > 0.0 && cg_tol < 1.0)) return fail(c, MCD_E_INVALID, "cg_tol must be in (0, 1)");
+  try {
+    return green_gradient(c, site, spin, L, n_block_iter, w_t, z_re, z_im, nz, g_re, g_im, grad_t, grad_eps, grad_U,
+                          cg_tol, cg_iters);
+  } catch (const std::bad_alloc&) {
+    return fail(c, MCD_E_OOM, "Green gradient: out of host memory");
+  }
+}
+
 int mcd_symeig(int n, const double* A, double* w, int rows, double* X) {
   if (n < 0 || (n > 0 && (!A || !w)) || rows < 0) return MCD_E_INVALID;
   if (n == 0) return MCD_OK;

@@ -223,6 +223,11 @@ int batch_apply(mcd_ctx* const* ctxs, int n, const void* x, void* y, int dtype);
 int batch_lanczos_ground(mcd_ctx* const* ctxs, int n, int max_iter, double tol, uint64_t seed, int dtype,
                          double* E0, int* iters, double* resid, void* const* psi);
 
+// gradient of the Green function (band.cu)
+int green_gradient(mcd_ctx* c, const int* site, const int* spin, int L, int n_blocks, double w_t,
+                   const double* z_re, const double* z_im, int nz, const double* g_re, const double* g_im,
+                   double* grad_t, double* grad_eps, double* grad_U, double cg_tol, int* cg_iters);
+
 // device index (index.cu)
 int build_index(mcd_ctx* c, const uint64_t* words, int64_t n, bool on_device);
 // exclusive scan of n uint32 values (in may equal out), stream-ordered
