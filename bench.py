@@ -12,8 +12,12 @@ value   = H~ v connections processed per second (nnz_offdiag(H~) x 200 per
           step, all ranks) with the basis already in HBM;
 e2e     = the same through the C ABI from host words: mcd_set_basis (copy in,
           index) + mcd_lanczos_ground + E0 back to the host, every step;
-roofline: the H~ v pair of kernels, algorithmic bytes N_f (8 + 2 L s) per
-          application over their mean CUDA-event duration in the timed steps.
+roofline: the H~ v pair of kernels (the cached-record kernels: the first
+          H~ v of each step's basis enumerates and looks up every hop once and
+          stores the found ones, the later ones stream them), algorithmic
+          bytes N_f (8 + 2 L s) per application over their mean CUDA-event
+          duration in the timed steps; the record bytes they also read are
+          reported beside it.
 
 --impl reference times the oracle (the CPU fp64 implementation that the tests
 check the kernels against) on a bounded sample of the same workload.
@@ -187,7 +191,7 @@ def traffic_for(kernel_key: str):
     if not ent:
         return None
     h = hashlib.sha256()
-    for f in ("hv.cu", "hv_common.cuh"):
+    for f in ("hv_cache.cu", "hv_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2509_22975_gb300", "csrc", f), "rb").read())
     return ent["bytes_per_launch"] if ent.get("kernel_src_sha") == h.hexdigest()[:16] else None
 
@@ -242,10 +246,28 @@ def impurity_batch(pkg, dev, n_inst=256, steps=400, tol=1e-6):
     return out
 
 
+def cache_build_ms(pkg, ctx, n, dev):
+    """Time of the first H~v of a basis (record build + one application)
+    minus that of the next one (CUDA events, one column fp32)."""
+    import torch
+    x = torch.randn(n, dtype=torch.float32, device=dev)
+    y = torch.empty_like(x)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    ctx.mcd_apply(x, y)
+    ev[1].record()
+    ctx.mcd_apply(x, y)
+    ev[2].record()
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]) - ev[1].elapsed_time(ev[2])
+
+
 def rect24_hv(pkg, configs, dev, peak, cols=(1, 24, 48), reps=5):
     """H~V on the 6x4 t-t' cluster (24 sites, 11 + 11 electrons, Monte Carlo
-    basis of 5e7 states, hash-lookup kernels), fp32, each width timed alone
-    with CUDA events after warm-up; X and Y are far larger than L2."""
+    basis of 5e7 states), fp32, each width timed alone with CUDA events after
+    warm-up; X and Y are far larger than L2.  The first H~v builds the
+    connection records (timed separately: build_ms)."""
     import torch
     w = configs.rect24_u8()
     ctx = pkg.Context(dev.index or 0)
@@ -253,10 +275,13 @@ def rect24_hv(pkg, configs, dev, peak, cols=(1, 24, 48), reps=5):
     t0 = time.perf_counter()
     ctx.mcd_build_basis(w.seed, w.n_f, w.beta, [w.seed_word()])
     t_sample = time.perf_counter() - t0
+    n = ctx.mcd_basis_info(nnz=False)["n_states"]
+    build_ms = cache_build_ms(pkg, ctx, n, dev)
     info = ctx.mcd_basis_info()
-    n, nnz = info["n_states"], info["nnz_offdiag"]
+    nnz = info["nnz_offdiag"]
     res = {"workload": "rect6x4_tp-0.3_U8_Nup11_Ndn11_mcbasis5e7", "n_states": n, "nnz_offdiag": nnz,
-           "n_up_blocks": info["n_up_blocks"], "sampler_s": t_sample}
+           "n_up_blocks": info["n_up_blocks"], "sampler_s": t_sample, "hv_cache": ctx.mcd_hv_cache_info(),
+           "cache_build_ms": build_ms}
     for L_ in cols:
         x = torch.randn(n, L_, dtype=torch.float32, device=dev)
         y = torch.empty_like(x)
@@ -371,11 +396,16 @@ def main():
     alg_bytes = n * (8 + 2 * 1 * 4)
     peak, peak_src = measured_peak()
     achieved = alg_bytes / ((tA + tB) * 1e-3) / 1e9
-    tb, ta = traffic_for("hv_pass_B_square16_fp32_L1"), traffic_for("hv_pass_A_square16_fp32_L1")
+    tb, ta = traffic_for("hv_cached_pass_B_square16_fp32_L1"), traffic_for("hv_cached_pass_A_square16_fp32_L1")
+    cinfo = ctx.mcd_hv_cache_info()
+    rec_bytes = cinfo["bytes"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tb + ta) if (tb is not None and ta is not None) else None,
-                "kernel": "H~v pair (hv_l1_kernel pass B + pass A), one application",
+                "kernel": "H~v pair (hv_cached_kernel pass B + pass A, records of the found hops), one application",
                 "algorithmic_bytes": alg_bytes, "peak_source": peak_src,
+                "record_bytes": rec_bytes,
+                "achieved_incl_records": (alg_bytes + rec_bytes) / ((tA + tB) * 1e-3) / 1e9,
+                "frac_incl_records": (alg_bytes + rec_bytes) / ((tA + tB) * 1e-3) / 1e9 / peak,
                 "mean_ms": {"pass_B": tB, "pass_A": tA, "krylov_update": tU},
                 "share_of_step": {"pass_B": kms[0] / args.steps / ms, "pass_A": kms[1] / args.steps / ms,
                                   "krylov_update": kms[2] / args.steps / ms}}
@@ -395,6 +425,10 @@ def main():
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
            "path": "mcd_set_basis(host words) + mcd_lanczos_ground + E0 to host"}
 
+    # the record build alone: a fresh basis, first H~v minus the next one
+    ctx.mcd_set_basis_device(words_dev)
+    build_ms = cache_build_ms(pkg, ctx, n, dev)
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic: Monte Carlo basis sampled by the library",
@@ -402,6 +436,7 @@ def main():
            "gpu_launches": launches, "clocks": clocks,
            "basis": {"n_states": n, "nnz_offdiag": nnz, "n_up_blocks": info["n_up_blocks"],
                      "n_dn_blocks": info["n_dn_blocks"], "sampler_s": t_sample},
+           "hv_cache": dict(cinfo, build_ms=build_ms),
            "E0_fp32": r32["E0"], "lanczos_iters_per_s_fp32": r32["iters"] / (ms * 1e-3)}
 
     if args.hv_cols:

@@ -74,6 +74,18 @@ typedef enum { MCD_F64 = 0, MCD_F32 = 1 } mcd_dtype;
                                    host threads (default); 1 = host threads;
                                    2 = GPU (MCD_E_INVALID when not possible).
                                    Both give the same basis, word for word. */
+#define MCD_OPT_HV_CACHE 6       /* connection cache of H*v: 0 = the first
+                                   H*v of a basis (and Hamiltonian) runs the
+                                   matrix-free enumeration and lookup once and
+                                   keeps the found hops in device memory
+                                   (2 or 4 bytes each), later H*v stream them,
+                                   when they fit in half the free memory
+                                   (default); 1 = off (every H*v enumerates
+                                   and looks up, nothing stored); 2 = required
+                                   (mcd_apply fails when the records cannot be
+                                   built).  Only with MCD_OPT_HV_ALGO = 0.
+                                   The result is the same matrix, summed in
+                                   another order (within rounding). */
 #define MCD_OPT_HASH_ITEM 4     /* states per work item of the hash-lookup
                                    kernels: a power of two in [64, 4096]
                                    (default 1024).  Blocks of more states are
@@ -285,6 +297,17 @@ int mcd_lanczos_coeffs(const mcd_ctx* ctx, double* a, double* b, int cap, int* m
  * (0 = dn-major up-hop pass, 1 = up-major dn-hop + diagonal pass,
  *  2 = Krylov update, 3 = plain kernel).  reset != 0 clears after reading. */
 int mcd_kernel_times(mcd_ctx* ctx, double* ms, int64_t* count, int n_classes, int reset);
+
+/* Connection cache of the current basis and Hamiltonian (MCD_OPT_HV_CACHE):
+ * *bytes = device bytes of its records including padding, *n_conn = stored
+ * hops (both passes; equals the off-diagonal nonzeros of H~), *rec_bytes =
+ * bytes per record (2: items whose blocks hold at most 16383 states take
+ * 2-byte records, larger ones 4; 4: every item), all 0 when no cache is
+ * built; *wait_errors = 1 when a bounded wait inside a cached H*v kernel ran
+ * out since the records were built (its results are then not to be used).
+ * Any pointer may be NULL.  Synchronises the context's stream.  MCD_E_STATE
+ * without a basis. */
+int mcd_hv_cache_info(mcd_ctx* ctx, int64_t* bytes, int64_t* n_conn, int* rec_bytes, int* wait_errors);
 
 /* Number of kernels this context has launched since creation (all entry
  * points); *n receives the count. */

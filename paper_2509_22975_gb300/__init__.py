@@ -21,6 +21,8 @@ MCD_F64, MCD_F32 = 0, 1
 MCD_SAMPLE_NEW_ONLY = 1
 MCD_OPT_HV_ALGO, MCD_OPT_KERNEL_TIMING, MCD_OPT_SAMPLER_THREADS, MCD_OPT_HASH_ITEM = 1, 2, 3, 4
 MCD_OPT_SAMPLER_DEVICE = 5
+MCD_OPT_HV_CACHE = 6
+CACHE_AUTO, CACHE_OFF, CACHE_REQUIRED = 0, 1, 2
 SAMPLER_AUTO, SAMPLER_HOST, SAMPLER_DEVICE = 0, 1, 2
 HV_AUTO, HV_PLAIN, HV_SEARCH, HV_HASH = 0, 1, 2, 3
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mcd.h")
@@ -46,6 +48,8 @@ _SIGS = {
     "mcd_set_basis_device": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64]),
     "mcd_get_basis": (ctypes.c_int, [c_vp, c_u64p, ctypes.c_int64, c_i64p]),
     "mcd_launch_count": (ctypes.c_int, [c_vp, c_i64p]),
+    "mcd_hv_cache_info": (ctypes.c_int, [c_vp, c_i64p, c_i64p, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int)]),
     "mcd_basis_info": (ctypes.c_int, [c_vp, c_i64p, c_i64p, c_i64p, c_i64p]),
     "mcd_apply": (ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mcd_diagonal": (ctypes.c_int, [c_vp, c_vp]),
@@ -244,6 +248,16 @@ class Context:
         out = np.empty(n.value, dtype=np.uint64)
         self._check(self.L.mcd_get_basis(self.h, out.ctypes.data_as(c_u64p), len(out), ctypes.byref(n)))
         return out
+
+    def mcd_hv_cache_info(self) -> dict:
+        """Connection cache of the current basis: record bytes (with padding),
+        stored hops, bytes per record (zeros when none is built) and whether a
+        bounded wait in a cached kernel ran out."""
+        b, n, r, w = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int(0), ctypes.c_int(0)
+        self._sync_stream()
+        self._check(self.L.mcd_hv_cache_info(self.h, ctypes.byref(b), ctypes.byref(n), ctypes.byref(r),
+                                             ctypes.byref(w)))
+        return {"bytes": b.value, "n_conn": n.value, "rec_bytes": r.value, "wait_errors": w.value}
 
     def mcd_basis_info(self, nnz: bool = True) -> dict:
         v = [ctypes.c_int64(0) for _ in range(4)]

@@ -1238,6 +1238,12 @@ int hv_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, d
     ticket = c->lw.ticket;
     dot_out = c->lw.scal + dot_slot;
   }
+  if (c->hv_algo == 0 && c->hv_cache != 1) {
+    bool used = false;
+    const int st = cache_apply(c, x, y, ncols, ld, dtype, dot_partials, dot_partials ? c->lw.max_ctas : 0, ticket,
+                               dot_out, &used);
+    if (st != MCD_OK || used) return st;
+  }
   if (hash_eligible(c))
     return hash_apply(c, x, y, ncols, ld, dtype, dot_partials, dot_partials ? c->lw.max_ctas : 0, ticket, dot_out);
   const bool vec_ok = [&] {

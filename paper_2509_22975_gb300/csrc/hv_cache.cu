@@ -1,0 +1,1217 @@
+// Connection cache of y = H~ x.
+//
+// The nonzeros of the projected matrix H~ are the hops whose targets are in
+// the basis (App. B: targets outside F~ are discarded).  They depend only on
+// the basis and the Hamiltonian, so Lanczos (hundreds of H~x with the same
+// H~) and band Lanczos (hundreds of H~V) would otherwise enumerate and look
+// up the same hops every step.  The first H~x of a basis runs the
+// enumeration and the in-block lookup of both passes once (the bond loop,
+// masked-popcount sign and in-block binary search of the matrix-free block
+// kernels) and writes what it finds as records:
+//   2 bytes  position:14 | sign:1 | amplitude class:1   (<= 2 amplitudes)
+//   4 bytes  position:22 | sign:1 | class:9             (otherwise, or an
+//            item whose blocks hold more than 16383 states)
+// where position is the target's place in its work item's stage range (the
+// blocks of the item), so that x of the range can be staged in shared
+// memory.  Later H~x stream the records and gather from the staged rows.
+//
+// Layout of the records: the states of a work item are sorted by their
+// number of records (most first; equal counts in position order) and form
+// slices of 32; group g of a slice holds, for each lane l, the records
+// 8g..8g+7 (2-byte) or 4g..4g+3 (4-byte) of the lane's state, all ones past
+// its last record.  A slice has as many groups as its longest list needs
+// (sliced ELL with sorting inside the item), so one warp reads one slice
+// with every load aligned, little padding and no per-state offsets.
+//
+// Sums keep the arithmetic of the matrix-free kernels: per state, hops of
+// one amplitude class are summed first, then multiplied by the class's fp64
+// amplitude (split into two floats for fp32 vectors).
+//
+// One column (Lanczos): a persistent warp-specialised kernel.  One producer
+// thread moves each item's records, lane map, slice offsets, staged x rows
+// and per-state words into shared memory with bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier), two stages deep,
+// while eight consumer warps work on the previous item from shared memory
+// and only store to global memory.  Pass B reads x in its own (dn-major)
+// order from a permuted copy, so that its rows are contiguous, and writes
+// its part of y to a scratch vector that pass A streams in.
+// Many columns (band Lanczos): CTAs stage x rows of an item with ordinary
+// loads and groups of G lanes share a state.
+#include <algorithm>
+#include <vector>
+
+#include "hv_common.cuh"
+
+namespace mcd {
+namespace {
+
+constexpr int kCT = 256;                     // threads of the build and multi-column kernels
+constexpr int kCWarps = kCT / 32;
+constexpr int kCItem = 512;                  // states per work item (at most, unless one block is larger)
+constexpr int kGroup = 512;                  // bytes of one record group: 32 lanes x 16 bytes
+constexpr int kSliceMap = 64;                // bytes of a slice's lane map (32 x u16)
+constexpr uint16_t kNoState = 0xFFFFu;
+constexpr int kBuildStageWords = 12288;      // minor words staged by the build kernels (48 KiB)
+constexpr int kMStageBytes = 48 * 1024;      // staged x rows of the multi-column kernel
+constexpr int kMaxCount = 512;               // records of one state in one pass (n_bonds <= 496)
+// streaming one-column kernel
+constexpr int kSConsumers = 8;
+constexpr int kSThreads = 32 * (kSConsumers + 1);
+constexpr int kSStages = 2;
+constexpr int kSRecBytes = 24 * 1024;        // records of one item per stage
+constexpr int kSMapBytes = (kCItem / 32) * kSliceMap;
+constexpr int kSColBytes = 128;              // slice offsets of an item (17 + alignment)
+constexpr int kSXBytes = 16 * 1024 + 32;     // staged x rows per stage (+ alignment slack)
+constexpr int kSAuxBytes = kCItem * 8 + 16;  // basis word (pass A) or basis index (pass B) of each state
+constexpr int kSAux2Bytes = kCItem * 8 + 16; // pass B's part of y (pass A)
+constexpr int kSOffMap = kSRecBytes;
+constexpr int kSOffCol = kSOffMap + kSMapBytes;
+constexpr int kSOffX = kSOffCol + kSColBytes;
+constexpr int kSOffAux = kSOffX + kSXBytes;
+constexpr int kSOffAux2 = kSOffAux + kSAuxBytes;
+constexpr int kSStageBytes = kSOffAux2 + kSAux2Bytes;
+static_assert(kSStageBytes % 16 == 0 && kSOffX % 16 == 0 && kSOffAux % 16 == 0 && kSOffAux2 % 16 == 0,
+              "stage buffers on 16-byte boundaries");
+constexpr uint32_t kSpinLimit = 1u << 22;    // polls of an mbarrier before a wait gives up
+
+template <typename R>
+struct Rec;
+template <>
+struct Rec<uint16_t> {
+  static constexpr int kPer = 8;                 // records per lane per group
+  static constexpr uint32_t kSent = 0xFFFFu;     // padding
+  static constexpr uint32_t kMaxStage = 0x3FFFu; // positions 0 .. 0x3FFE (0x3FFF + sign + class 1 = padding)
+  static constexpr int kMaxCls = 2;
+  __host__ __device__ static uint32_t make(uint32_t q, uint32_t neg, uint32_t cls) {
+    return q | (neg << 14) | (cls << 15);
+  }
+  __device__ static uint32_t pos(uint32_t r) { return r & 0x3FFFu; }
+  __device__ static bool neg(uint32_t r) { return (r >> 14) & 1u; }
+  __device__ static uint32_t cls(uint32_t r) { return r >> 15; }
+};
+template <>
+struct Rec<uint32_t> {
+  static constexpr int kPer = 4;
+  static constexpr uint32_t kSent = 0xFFFFFFFFu;
+  static constexpr uint32_t kMaxStage = 0x3FFFFFu;
+  static constexpr int kMaxCls = 512;
+  __host__ __device__ static uint32_t make(uint32_t q, uint32_t neg, uint32_t cls) {
+    return q | (neg << 22) | (cls << 23);
+  }
+  __device__ static uint32_t pos(uint32_t r) { return r & 0x3FFFFFu; }
+  __device__ static bool neg(uint32_t r) { return (r >> 22) & 1u; }
+  __device__ static uint32_t cls(uint32_t r) { return r >> 23; }
+};
+
+struct CArgs {
+  const void* x;
+  void* y;
+  const void* xb;                // pass B of the streaming kernel: x in layout order
+  void* yb;                      // streaming kernels: pass B's part of y (basis order), read by pass A
+  int ncols, ld;
+  int ncp;                       // staged row stride (elements)
+  int xs_cap;                    // staged elements (multi-column) / minor words (build)
+  int off_xs;                    // byte offset of the staging area in dynamic shared memory
+  int n_sites;
+  int64_t n;                     // states
+  int64_t x_bytes;               // bytes of x the streaming kernel may read from its base
+  const uint64_t* words;         // basis words (diagonal of pass A)
+  const uint32_t* minor;
+  const uint32_t* blk_off;
+  const uint32_t* perm;          // pass B: layout position -> basis index
+  const CItem* items;
+  int64_t n_items;
+  const uint32_t* col;           // [n_slices + 1] first record group of each slice
+  const uint16_t* smap;          // [n_slices * 32] lane -> state of the item
+  void* rec;
+  const double* c64;             // [n_cls]
+  const float* chi;
+  const float* clo;
+  int n_cls;
+  double* dot_partials;
+  unsigned int* ticket;
+  double* dot_out;
+  unsigned int* err;
+  // build
+  const uint16_t* bond_cls;      // [n_bonds] record class of each bond
+  uint16_t* cnt;                 // [n] records of each state
+  uint32_t* wid;                 // [n_slices] groups of each slice
+  uint16_t* smap_out;
+  unsigned long long* nconn;     // found hops
+};
+
+// ---- build ------------------------------------------------------------------------
+
+// Enumeration of the found hops of state k (layout position) of an item,
+// in bond order; f(j, target position, sign, bond) is called for the j-th
+// one.  mn = minor words of the stage range (staged or in global memory).
+template <typename F>
+__device__ __forceinline__ uint32_t enumerate_state(const CArgs& a, const HamParams& hp, const CItem& it,
+                                                    uint32_t sb, const uint32_t* mn, uint32_t k, F f) {
+  uint32_t b = it.b0;
+  if (it.b1 > it.b0) {   // block of k among b0..b1
+    uint32_t lo = it.b0, len = it.b1 - it.b0 + 1;
+    while (len > 1) {
+      const uint32_t h = len >> 1;
+      if (a.blk_off[lo + h] <= k) lo += h;
+      len -= h;
+    }
+    b = lo;
+  }
+  const int bs = int(a.blk_off[b] - sb), be = int(a.blk_off[b + 1] - sb);
+  const uint32_t m = mn[k - sb];
+  uint32_t cnt = 0;
+  for (int bi = 0; bi < hp.n_bonds; ++bi) {
+    const uint32_t mk = hp.bonds[bi].mask;
+    if (__popc(m & mk) != 1) continue;
+    const int q = find_sorted(mn, bs, be, m ^ mk);
+    if (q < 0) continue;
+    f(cnt, uint32_t(q), __popc(m & hp.bonds[bi].between) & 1u, bi);
+    ++cnt;
+  }
+  return cnt;
+}
+
+__device__ __forceinline__ const uint32_t* stage_minor(const CArgs& a, const CItem& it, uint32_t* s_minor,
+                                                       uint32_t& sb) {
+  sb = a.blk_off[it.b0];
+  const uint32_t se = a.blk_off[it.b1 + 1];
+  const int nst = int(se - sb);
+  const bool staged = nst <= a.xs_cap;
+  __syncthreads();
+  if (staged)
+    for (int q = threadIdx.x; q < nst; q += blockDim.x) s_minor[q] = a.minor[sb + q];
+  __syncthreads();
+  return staged ? s_minor : a.minor + sb;
+}
+
+// cnt[k] = records of state k; nconn += all of them
+__global__ void __launch_bounds__(kCT) cache_count_kernel(const CArgs a, const HamParams hp) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  uint32_t* s_minor = reinterpret_cast<uint32_t*>(s_dyn);
+  unsigned long long nc = 0;
+  for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const CItem it = a.items[item];
+    uint32_t sb;
+    const uint32_t* mn = stage_minor(a, it, s_minor, sb);
+    for (uint32_t k = it.lo + threadIdx.x; k < it.hi; k += kCT) {
+      const uint32_t c = enumerate_state(a, hp, it, sb, mn, k, [](uint32_t, uint32_t, uint32_t, int) {});
+      a.cnt[k] = uint16_t(c);
+      nc += c;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nc += __shfl_xor_sync(0xffffffffu, nc, o);
+  if ((threadIdx.x & 31) == 0 && nc) atomicAdd(a.nconn, nc);
+}
+
+// Per item: states sorted by count, most first, equal counts in position
+// order (a stable counting sort by one warp: ranks among equal counts by
+// __match_any); smap and the groups of each slice.
+__global__ void __launch_bounds__(kCT) cache_sort_kernel(const CArgs a) {
+  __shared__ uint32_t s_off[kMaxCount];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const CItem it = a.items[item];
+    const int ns = int(it.hi - it.lo);
+    const int nsl = (ns + 31) / 32;
+    const int per = (it.flags & 1u) ? Rec<uint32_t>::kPer : Rec<uint16_t>::kPer;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kMaxCount; i += kCT) s_off[i] = 0u;
+    __syncthreads();
+    for (int j = threadIdx.x; j < ns; j += kCT) atomicAdd(&s_off[a.cnt[it.lo + j]], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {   // exclusive offsets, largest count first
+      uint32_t run = 0;
+      for (int c = kMaxCount - 1; c >= 0; --c) {
+        const uint32_t v = s_off[c];
+        s_off[c] = run;
+        run += v;
+      }
+    }
+    __syncthreads();
+    uint16_t* sm = a.smap_out + int64_t(it.slice0) * 32;
+    if (warp == 0) {
+      for (int base = 0; base < ns; base += 32) {
+        const int j = base + lane;
+        const uint32_t c = j < ns ? a.cnt[it.lo + j] : uint32_t(kMaxCount);   // kMaxCount: no state
+        const uint32_t peers = __match_any_sync(0xffffffffu, c);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        const uint32_t p = c < uint32_t(kMaxCount) ? s_off[c] + rank : 0u;
+        __syncwarp();
+        if (c < uint32_t(kMaxCount) && (peers >> lane) == 1u) s_off[c] += __popc(peers);   // highest peer
+        __syncwarp();
+        if (j < ns) sm[p] = uint16_t(j);
+      }
+    }
+    __syncthreads();
+    for (int p = ns + threadIdx.x; p < nsl * 32; p += kCT) sm[p] = kNoState;
+    __syncthreads();
+    for (int sl = threadIdx.x; sl < nsl; sl += kCT) {
+      const uint32_t c = a.cnt[it.lo + sm[sl * 32]];   // the slice's first state has the most records
+      a.wid[it.slice0 + sl] = (c + per - 1) / per;
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void write_state(const CArgs& a, const HamParams& hp, const uint16_t* s_cls,
+                                            const CItem& it, uint32_t sb, const uint32_t* mn, int64_t s,
+                                            int lane, uint16_t loc) {
+  constexpr int kRow = kGroup / int(sizeof(R));
+  const uint32_t g0 = a.col[s];
+  const int width = int(a.col[s + 1] - g0) * Rec<R>::kPer;
+  R* base = static_cast<R*>(a.rec) + int64_t(g0) * kRow + lane * Rec<R>::kPer;
+  auto put = [&](uint32_t j, uint32_t r) {
+    if (int(j) < width) base[int64_t(j / Rec<R>::kPer) * kRow + (j % Rec<R>::kPer)] = R(r);
+  };
+  uint32_t cnt = 0;
+  if (loc != kNoState)
+    cnt = enumerate_state(a, hp, it, sb, mn, it.lo + loc, [&](uint32_t j, uint32_t q, uint32_t ng, int bi) {
+      put(j, Rec<R>::make(q, ng, s_cls[bi]));
+    });
+  for (int j = int(cnt); j < width; ++j) put(uint32_t(j), Rec<R>::kSent);
+}
+
+__global__ void __launch_bounds__(kCT) cache_write_kernel(const CArgs a, const HamParams hp) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  uint32_t* s_minor = reinterpret_cast<uint32_t*>(s_dyn);
+  __shared__ uint16_t s_cls[kMaxBonds];
+  for (int i = threadIdx.x; i < hp.n_bonds; i += kCT) s_cls[i] = a.bond_cls[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const CItem it = a.items[item];
+    uint32_t sb;
+    const uint32_t* mn = stage_minor(a, it, s_minor, sb);
+    const int nsl = int((it.hi - it.lo + 31) / 32);
+    for (int sl = warp; sl < nsl; sl += kCWarps) {
+      const int64_t s = int64_t(it.slice0) + sl;
+      const uint16_t loc = a.smap[s * 32 + lane];
+      if (it.flags & 1u)
+        write_state<uint32_t>(a, hp, s_cls, it, sb, mn, s, lane, loc);
+      else
+        write_state<uint16_t>(a, hp, s_cls, it, sb, mn, s, lane, loc);
+    }
+  }
+}
+
+// ---- apply --------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T coef_hi(const double* c64, const float* chi, int c) {
+  return sizeof(T) == 4 ? T(chi[c]) : T(c64[c]);
+}
+template <typename T>
+__device__ __forceinline__ T coef_lo(const float* clo, int c) {
+  return sizeof(T) == 4 ? T(clo[c]) : T(0);
+}
+
+// acc += sum over the records of one state of t_class sign x[target] (VEC
+// columns).  rp = the lane's 16 bytes in the state's first group (shared or
+// global memory); ng groups, 512 bytes apart.  gather(q, v) loads the VEC
+// values of stage row q.  kU groups are loaded before any is used.
+template <typename T, typename R, int VEC, int kU, typename Gather>
+__device__ __forceinline__ void state_sum(const unsigned char* rp, int ng, int n_cls, const double* c64,
+                                          const float* chi, const float* clo, Gather gather, Acc<T> (&acc)[VEC]) {
+  using RR = Rec<R>;
+  T s0[VEC], s1[VEC];
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) s0[u] = s1[u] = T(0);
+  int cur = -1;   // class of the running sum (4-byte records)
+  for (int gb = 0; gb < ng; gb += kU, rp += kU * kGroup) {
+    uint4 pks[kU];
+#pragma unroll
+    for (int v = 0; v < kU; ++v)
+      pks[v] = gb + v < ng ? *reinterpret_cast<const uint4*>(rp + v * kGroup) : make_uint4(~0u, ~0u, ~0u, ~0u);
+#pragma unroll
+    for (int v = 0; v < kU; ++v) {
+      const uint4 pk = pks[v];
+      uint32_t r[RR::kPer];
+      if constexpr (sizeof(R) == 2) {
+        const uint32_t w[4] = {pk.x, pk.y, pk.z, pk.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          r[2 * h] = w[h] & 0xFFFFu;
+          r[2 * h + 1] = w[h] >> 16;
+        }
+      } else {
+        r[0] = pk.x;
+        r[1] = pk.y;
+        r[2] = pk.z;
+        r[3] = pk.w;
+      }
+      if (r[0] == RR::kSent) continue;   // padding is trailing: the rest of the group is padding
+      T xv[RR::kPer][VEC];
+#pragma unroll
+      for (int h = 0; h < RR::kPer; ++h)
+        if (r[h] != RR::kSent) gather(int(RR::pos(r[h])), xv[h]);
+#pragma unroll
+      for (int h = 0; h < RR::kPer; ++h) {
+        if (r[h] == RR::kSent) continue;
+        const bool ng_ = RR::neg(r[h]);
+        if constexpr (sizeof(R) == 2) {
+          if (RR::cls(r[h])) {
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) s1[u] += ng_ ? -xv[h][u] : xv[h][u];
+          } else {
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) s0[u] += ng_ ? -xv[h][u] : xv[h][u];
+          }
+        } else {
+          const int cl = int(RR::cls(r[h]));
+          if (cl != cur) {
+            if (cur >= 0) {
+              const T ch = coef_hi<T>(c64, chi, cur), cl_ = coef_lo<T>(clo, cur);
+#pragma unroll
+              for (int u = 0; u < VEC; ++u) {
+                acc[u].fma(ch, cl_, s0[u]);
+                s0[u] = T(0);
+              }
+            }
+            cur = cl;
+          }
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) s0[u] += ng_ ? -xv[h][u] : xv[h][u];
+        }
+      }
+    }
+  }
+  if constexpr (sizeof(R) == 2) {
+    if (n_cls > 0) {
+      const T ch = coef_hi<T>(c64, chi, 0), cl_ = coef_lo<T>(clo, 0);
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) acc[u].fma(ch, cl_, s0[u]);
+    }
+    if (n_cls > 1) {
+      const T ch = coef_hi<T>(c64, chi, 1), cl_ = coef_lo<T>(clo, 1);
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) acc[u].fma(ch, cl_, s1[u]);
+    }
+  } else if (cur >= 0) {
+    const T ch = coef_hi<T>(c64, chi, cur), cl_ = coef_lo<T>(clo, cur);
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) acc[u].fma(ch, cl_, s0[u]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ Coef<T> diag_of(const HamParams& hp, const float* dhi, const float* dlo,
+                                           const double* d64, uint32_t up, uint32_t dn) {
+  if (hp.uniform) {
+    const int nu = __popc(up & dn);
+    return Coef<T>{sizeof(T) == 4 ? T(dhi[nu]) : T(d64[nu]), sizeof(T) == 4 ? T(dlo[nu]) : T(0)};
+  }
+  return diag_coef<T>(hp, up, dn);
+}
+
+// Fixed-order <x, y> of pass A: CTA partials, then the last CTA sums them.
+template <int kWarps>
+__device__ __forceinline__ void dot_reduce(const CArgs& a, double dot_acc, double* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dot_acc += __shfl_xor_sync(0xffffffffu, dot_acc, o);
+  __syncthreads();
+  if (lane == 0) s_red[warp] = dot_acc;
+  __syncthreads();
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < kWarps; ++w) sum += s_red[w];
+    a.dot_partials[blockIdx.x] = sum;
+    __threadfence();
+    const unsigned tk = atomicAdd(a.ticket, 1u);
+    s_last = (tk == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    double sum = 0.0;
+    for (int i = threadIdx.x; i < int(gridDim.x); i += blockDim.x) sum += __ldcg(a.dot_partials + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    __syncthreads();
+    if (lane == 0) s_red[warp] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < kWarps; ++w) tot += s_red[w];
+      *a.dot_out = tot;
+      *a.ticket = 0u;
+    }
+  }
+}
+
+// ---- mbarrier and bulk copy (PTX) -----------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// waits for the phase of the given parity; false when kSpinLimit polls were not enough
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// One column, persistent and warp-specialised (see the top of the file).
+// Items of this CTA: blockIdx.x + i gridDim.x.  Stage i % kSStages holds
+// item i: its records, lane map, slice offsets, the x rows of its stage
+// range and, per state, the basis word and pass B's part of y (pass A) or
+// the basis index (pass B), each copied as whole aligned 16-byte units that
+// cover the range.  full[st] completes when the bytes have landed (or the
+// producer has marked the item direct: consumers then read global memory),
+// empty[st] when the kSConsumers consumer warps are done with it.
+template <typename T, bool PASS_A, bool DOT>
+__global__ void __launch_bounds__(kSThreads, 2) hv_stream_kernel(const CArgs a, const HamParams hp) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __shared__ __align__(8) uint64_t s_full[kSStages], s_empty[kSStages];
+  __shared__ int s_direct[kSStages], s_xoff[kSStages], s_coff[kSStages], s_aoff[kSStages], s_boff[kSStages];
+  __shared__ float s_dhi[kMaxSites + 1], s_dlo[kMaxSites + 1];
+  __shared__ double s_d64[kMaxSites + 1];
+  __shared__ double s_red[kSConsumers + 1];
+  double* s_c64 = reinterpret_cast<double*>(s_dyn + kSStages * kSStageBytes);
+  float* s_chi = reinterpret_cast<float*>(s_c64 + a.n_cls);
+  float* s_clo = s_chi + a.n_cls;
+  for (int i = threadIdx.x; i < a.n_cls; i += kSThreads) {
+    s_c64[i] = a.c64[i];
+    s_chi[i] = a.chi[i];
+    s_clo[i] = a.clo[i];
+  }
+  if (threadIdx.x <= kMaxSites) {
+    s_dhi[threadIdx.x] = hp.dtab_hi[threadIdx.x];
+    s_dlo[threadIdx.x] = hp.dtab_lo[threadIdx.x];
+    s_d64[threadIdx.x] = hp.dtab[threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSStages; ++s) {
+      mbar_init(&s_full[s], 1);
+      mbar_init(&s_empty[s], kSConsumers);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n_my = blockIdx.x < a.n_items ? (a.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const T* __restrict__ xg = static_cast<const T*>(PASS_A ? a.x : a.xb);   // rows in layout order
+  T* __restrict__ y = static_cast<T*>(a.y);
+  T* __restrict__ yb = static_cast<T*>(a.yb);                                // pass B's part of y
+  const unsigned char* recg = static_cast<const unsigned char*>(a.rec);
+  double dot_acc = 0.0;
+  bool failed = false;
+  int64_t issued[kSStages];   // producer: last item index issued into each stage (-1 none)
+  for (int s = 0; s < kSStages; ++s) issued[s] = -1;
+
+  if (warp == kSConsumers) {
+    // producer: one thread issues the copies of the CTA's items, in order
+    if (lane == 0) {
+      for (int64_t i = 0; i < n_my; ++i) {
+        const int st = int(i % kSStages);
+        if (!mbar_wait(&s_empty[st], uint32_t((i / kSStages) & 1) ^ 1u)) {
+          failed = true;
+          break;
+        }
+        const CItem it = a.items[blockIdx.x + i * gridDim.x];
+        const uint32_t sb = a.blk_off[it.b0], se = a.blk_off[it.b1 + 1];
+        const int nsl = int((it.hi - it.lo + 31) / 32);
+        const uint32_t g0 = a.col[it.slice0], g1 = a.col[it.slice0 + nsl];
+        const uint32_t rb = (g1 - g0) * uint32_t(kGroup);
+        const uint32_t mb = uint32_t(nsl) * kSliceMap;
+        // 16-byte units covering [first, last) elements of size es
+        auto span = [](int64_t first, int64_t last, int64_t es, int64_t& lo16, int64_t& hi16) {
+          lo16 = (first * es) & ~int64_t(15);
+          hi16 = (last * es + 15) & ~int64_t(15);
+        };
+        int64_t xlo, xhi, clo, chi, alo, ahi, blo = 0, bhi = 0;
+        span(sb, se, sizeof(T), xlo, xhi);
+        span(it.slice0, int64_t(it.slice0) + nsl + 1, 4, clo, chi);
+        if (PASS_A) {
+          span(it.lo, it.hi, 8, alo, ahi);            // basis words
+          span(it.lo, it.hi, sizeof(T), blo, bhi);    // pass B's part of y
+        } else {
+          span(it.lo, it.hi, 4, alo, ahi);            // basis index of each position
+        }
+        const bool direct = rb > uint32_t(kSRecBytes) || xhi - xlo > int64_t(kSXBytes) || xhi > a.x_bytes;
+        s_direct[st] = direct ? 1 : 0;
+        s_xoff[st] = int((int64_t(sb) * int64_t(sizeof(T)) - xlo) / int64_t(sizeof(T)));
+        s_coff[st] = int((int64_t(it.slice0) * 4 - clo) / 4);
+        s_aoff[st] = int((int64_t(it.lo) * (PASS_A ? 8 : 4) - alo) / (PASS_A ? 8 : 4));
+        s_boff[st] = int((int64_t(it.lo) * int64_t(sizeof(T)) - blo) / int64_t(sizeof(T)));
+        unsigned char* stage = s_dyn + st * kSStageBytes;
+        const uint32_t bytes =
+            direct ? 0u : rb + mb + uint32_t(chi - clo) + uint32_t(xhi - xlo) + uint32_t(ahi - alo) + uint32_t(bhi - blo);
+        if (bytes == 0u) {
+          mbar_arrive(&s_full[st]);
+        } else {
+          mbar_arrive_tx(&s_full[st], bytes);
+          if (rb) bulk_g2s(stage, recg + int64_t(g0) * kGroup, rb, &s_full[st]);
+          bulk_g2s(stage + kSOffMap, a.smap + int64_t(it.slice0) * 32, mb, &s_full[st]);
+          bulk_g2s(stage + kSOffCol, reinterpret_cast<const unsigned char*>(a.col) + clo, uint32_t(chi - clo),
+                   &s_full[st]);
+          if (xhi > xlo)
+            bulk_g2s(stage + kSOffX, reinterpret_cast<const unsigned char*>(xg) + xlo, uint32_t(xhi - xlo),
+                     &s_full[st]);
+          const unsigned char* aux =
+              PASS_A ? reinterpret_cast<const unsigned char*>(a.words) : reinterpret_cast<const unsigned char*>(a.perm);
+          bulk_g2s(stage + kSOffAux, aux + alo, uint32_t(ahi - alo), &s_full[st]);
+          if (PASS_A)
+            bulk_g2s(stage + kSOffAux2, reinterpret_cast<const unsigned char*>(yb) + blo, uint32_t(bhi - blo),
+                     &s_full[st]);
+        }
+        issued[st] = i;
+      }
+    }
+  } else {
+    // consumers
+    const uint32_t half = a.n_sites >= 32 ? 0xFFFFFFFFu : ((1u << a.n_sites) - 1u);
+    for (int64_t i = 0; i < n_my; ++i) {
+      const int st = int(i % kSStages);
+      if (!mbar_wait(&s_full[st], uint32_t((i / kSStages) & 1))) {
+        failed = true;
+        break;
+      }
+      const CItem it = a.items[blockIdx.x + i * gridDim.x];
+      const uint32_t sb = a.blk_off[it.b0];
+      const int nsl = int((it.hi - it.lo + 31) / 32);
+      const bool direct = s_direct[st] != 0;
+      const unsigned char* stage = s_dyn + st * kSStageBytes;
+      // per item: where each array of the item lives (stage, or global memory)
+      const uint32_t* colp = direct ? a.col + it.slice0
+                                    : reinterpret_cast<const uint32_t*>(stage + kSOffCol) + s_coff[st];
+      const uint32_t g0 = colp[0];
+      const unsigned char* recp = direct ? recg + int64_t(g0) * kGroup : stage;
+      const uint16_t* mapp =
+          direct ? a.smap + int64_t(it.slice0) * 32 : reinterpret_cast<const uint16_t*>(stage + kSOffMap);
+      const T* xs = direct ? xg + sb : reinterpret_cast<const T*>(stage + kSOffX) + s_xoff[st];
+      const uint64_t* wp = direct ? a.words + it.lo : reinterpret_cast<const uint64_t*>(stage + kSOffAux) + s_aoff[st];
+      const uint32_t* pp = direct ? a.perm + it.lo : reinterpret_cast<const uint32_t*>(stage + kSOffAux) + s_aoff[st];
+      const T* ybp = direct ? yb + it.lo : reinterpret_cast<const T*>(stage + kSOffAux2) + s_boff[st];
+      const bool wide = (it.flags & 1u) != 0u;
+      for (int sl = warp; sl < nsl; sl += kSConsumers) {
+        const uint16_t loc = mapp[sl * 32 + lane];
+        if (loc == kNoState) continue;
+        const uint32_t k = it.lo + loc;
+        const uint32_t ga = colp[sl], gz = colp[sl + 1];
+        const unsigned char* rp = recp + int64_t(ga - g0) * kGroup + lane * 16;
+        Acc<T> acc[1];
+        acc[0].zero();
+        auto gather = [&](int q, T* v) { v[0] = xs[q]; };
+        if (wide)
+          state_sum<T, uint32_t, 1, 4>(rp, int(gz - ga), a.n_cls, s_c64, s_chi, s_clo, gather, acc);
+        else
+          state_sum<T, uint16_t, 1, 4>(rp, int(gz - ga), a.n_cls, s_c64, s_chi, s_clo, gather, acc);
+        if (PASS_A) {
+          const uint64_t w = wp[loc];
+          const uint32_t up = uint32_t(w >> a.n_sites), dn = uint32_t(w) & half;
+          const T xk = xs[k - sb];
+          const Coef<T> dc = diag_of<T>(hp, s_dhi, s_dlo, s_d64, up, dn);
+          acc[0].fma(dc.hi, dc.lo, xk);
+          const T out = acc[0].value() + ybp[loc];
+          y[k] = out;
+          if constexpr (DOT) dot_acc += double(xk) * double(out);
+        } else {
+          yb[pp[loc]] = acc[0].value();
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s_empty[st]);
+    }
+  }
+  const int any_failed = __syncthreads_or(failed ? 1 : 0);
+  if (any_failed) {
+    if (warp == kSConsumers && lane == 0) {
+      // copies still in flight land before the CTA's shared memory is released
+      for (int s = 0; s < kSStages; ++s)
+        if (issued[s] >= 0) mbar_wait(&s_full[s], uint32_t((issued[s] / kSStages) & 1));
+    }
+    if (threadIdx.x == 0) atomicOr(a.err, 1u);
+    __syncthreads();
+  }
+  if constexpr (DOT) dot_reduce<kSConsumers + 1>(a, dot_acc, s_red);
+}
+
+// x in the layout's order: xb[k] = x[perm[k]] (one column, stride ld)
+template <typename T>
+__global__ void permute_kernel(const T* __restrict__ x, int ld, const uint32_t* __restrict__ perm, int64_t n,
+                               T* __restrict__ xb) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < n) xb[k] = x[int64_t(perm[k]) * ld];
+}
+
+// Many columns (or one column with a row stride): CTA per item, x rows of the
+// stage range staged with ordinary loads when they fit, G lanes per state.
+template <typename T, int VEC, int G, bool PASS_A>
+__global__ void __launch_bounds__(kCT) hv_cached_kernel(const CArgs a, const HamParams hp) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  double* s_c64 = reinterpret_cast<double*>(s_dyn);
+  float* s_chi = reinterpret_cast<float*>(s_c64 + a.n_cls);
+  float* s_clo = s_chi + a.n_cls;
+  T* xs = reinterpret_cast<T*>(s_dyn + a.off_xs);
+  __shared__ float s_dhi[kMaxSites + 1], s_dlo[kMaxSites + 1];
+  __shared__ double s_d64[kMaxSites + 1];
+  for (int i = threadIdx.x; i < a.n_cls; i += kCT) {
+    s_c64[i] = a.c64[i];
+    s_chi[i] = a.chi[i];
+    s_clo[i] = a.clo[i];
+  }
+  if (threadIdx.x <= kMaxSites) {
+    s_dhi[threadIdx.x] = hp.dtab_hi[threadIdx.x];
+    s_dlo[threadIdx.x] = hp.dtab_lo[threadIdx.x];
+    s_d64[threadIdx.x] = hp.dtab[threadIdx.x];
+  }
+  using C = ChunkOf<T, VEC>;
+  constexpr int kSPW = 32 / G;                   // states of a slice processed at once by a warp
+  constexpr int kU = VEC == 1 ? 4 : 1;           // record groups in flight per lane
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane % G, tg = lane / G;
+  const bool lane_ok = tg < kSPW;                // G not dividing 32 leaves lanes idle
+  const int col0 = g * VEC;
+  const int cvalid = a.ncols - col0;
+  const T* __restrict__ x = static_cast<const T*>(a.x);
+  T* __restrict__ y = static_cast<T*>(a.y);
+  const unsigned char* recg = static_cast<const unsigned char*>(a.rec);
+  const uint32_t half = a.n_sites >= 32 ? 0xFFFFFFFFu : ((1u << a.n_sites) - 1u);
+  const int ld = a.ld, ncp = a.ncp;
+
+  for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const CItem it = a.items[item];
+    const uint32_t sb = a.blk_off[it.b0], se = a.blk_off[it.b1 + 1];
+    const int nst = int(se - sb);
+    const bool staged = int64_t(nst) * ncp <= a.xs_cap;
+    __syncthreads();   // the previous item's rows are no longer read
+    if (staged && lane_ok && cvalid > 0) {
+      for (int q = warp * kSPW + tg; q < nst; q += kCWarps * kSPW) {
+        const int64_t row = PASS_A ? int64_t(sb) + q : int64_t(__ldg(a.perm + sb + q));
+        T v[VEC];
+        C::load(x + row * ld + col0, cvalid, v);
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) xs[q * ncp + col0 + u] = v[u];
+      }
+    }
+    __syncthreads();
+    const bool wide = (it.flags & 1u) != 0u;
+    auto gather = [&](int q, T* v) {
+      if (staged) {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) v[u] = xs[q * ncp + col0 + u];
+      } else {
+        const int64_t row = PASS_A ? int64_t(sb) + q : int64_t(__ldg(a.perm + sb + q));
+        C::load(x + row * ld + col0, cvalid, v);
+      }
+    };
+    const int nsl = int((it.hi - it.lo + 31) / 32);
+    for (int sl = warp; sl < nsl; sl += kCWarps) {
+      const int64_t s = int64_t(it.slice0) + sl;
+      const uint32_t ga = __ldg(a.col + s), gz = __ldg(a.col + s + 1);
+      if (!lane_ok || cvalid <= 0) continue;   // lanes past the last column chunk idle
+      for (int t = tg; t < 32; t += kSPW) {
+        const uint16_t loc = __ldg(a.smap + s * 32 + t);
+        if (loc == kNoState) break;            // empty lanes are the slice's last ones
+        const uint32_t k = it.lo + loc;
+        const unsigned char* rp = recg + int64_t(ga) * kGroup + t * 16;
+        Acc<T> acc[VEC];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) acc[u].zero();
+        if (wide)
+          state_sum<T, uint32_t, VEC, kU>(rp, int(gz - ga), a.n_cls, s_c64, s_chi, s_clo, gather, acc);
+        else
+          state_sum<T, uint16_t, VEC, kU>(rp, int(gz - ga), a.n_cls, s_c64, s_chi, s_clo, gather, acc);
+        T out[VEC];
+        if (PASS_A) {
+          const uint64_t w = __ldg(a.words + k);
+          const uint32_t up = uint32_t(w >> a.n_sites), dn = uint32_t(w) & half;
+          T xk[VEC], yk[VEC];
+          if (staged) {
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) xk[u] = xs[int(k - sb) * ncp + col0 + u];
+          } else {
+            C::load(x + int64_t(k) * ld + col0, cvalid, xk);
+          }
+          C::load(y + int64_t(k) * ld + col0, cvalid, yk);
+          const Coef<T> dc = diag_of<T>(hp, s_dhi, s_dlo, s_d64, up, dn);
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) {
+            acc[u].fma(dc.hi, dc.lo, xk[u]);
+            out[u] = acc[u].value() + yk[u];
+          }
+          C::store(y + int64_t(k) * ld + col0, cvalid, out);
+        } else {
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) out[u] = acc[u].value();
+          C::store(y + int64_t(__ldg(a.perm + k)) * ld + col0, cvalid, out);
+        }
+      }
+    }
+  }
+}
+
+// ---- host ------------------------------------------------------------------------
+
+cudaError_t grow_bytes(void*& p, int64_t& cap, int64_t need, cudaStream_t s) {
+  if (p && cap >= need) return cudaSuccess;
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMallocAsync(&p, size_t(std::max<int64_t>(need, 16)), s);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    return e;
+  }
+  cap = need;
+  return cudaSuccess;
+}
+template <typename P>
+cudaError_t grow(P*& p, int64_t& cap, int64_t need, size_t elem, cudaStream_t s) {
+  void* q = p;
+  int64_t cb = cap * int64_t(elem);
+  const cudaError_t e = grow_bytes(q, cb, need * int64_t(elem), s);
+  p = static_cast<P*>(q);
+  cap = e == cudaSuccess ? cb / int64_t(elem) : 0;
+  return e;
+}
+
+int sm_count(int dev) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  return v > 0 ? v : 1;
+}
+
+struct LayoutItems {
+  std::vector<CItem> items;
+  int64_t n_slices = 0, max_stage = 0;
+};
+
+// Work items of a layout: runs of whole blocks of at most kCItem states, or
+// pieces of kCItem states of a larger block.  wide_all: every item takes
+// 4-byte records; otherwise only items whose stage range is too long for
+// 14-bit positions.
+void make_items(const std::vector<uint32_t>& off, bool wide_all, LayoutItems& li) {
+  li.items.clear();
+  li.n_slices = 0;
+  li.max_stage = 0;
+  const int64_t nblk = int64_t(off.size()) - 1;
+  auto add = [&](uint32_t lo, uint32_t hi, uint32_t b0, uint32_t b1) {
+    const int64_t stage = int64_t(off[b1 + 1]) - off[b0];
+    const bool wide = wide_all || stage > int64_t(Rec<uint16_t>::kMaxStage);
+    li.items.push_back(CItem{lo, hi, b0, b1, uint32_t(li.n_slices), wide ? 1u : 0u});
+    li.n_slices += (hi - lo + 31) / 32;
+    li.max_stage = std::max(li.max_stage, stage);
+  };
+  int64_t b = 0;
+  while (b < nblk) {
+    const uint32_t bsz = off[b + 1] - off[b];
+    if (bsz > uint32_t(kCItem)) {
+      for (uint32_t p = off[b]; p < off[b + 1]; p += kCItem)
+        add(p, std::min<uint32_t>(p + kCItem, off[b + 1]), uint32_t(b), uint32_t(b));
+      ++b;
+      continue;
+    }
+    int64_t b1 = b;
+    while (b1 + 1 < nblk && off[b1 + 2] - off[b] <= uint32_t(kCItem)) ++b1;
+    add(off[b], off[b1 + 1], uint32_t(b), uint32_t(b1));
+    b = b1 + 1;
+  }
+}
+
+void fill_args(mcd_ctx* c, const Layout& L, CArgs& a) {
+  const ConnCache& cc = L.cc;
+  a = CArgs{};
+  a.n_sites = c->n;
+  a.n = L.n;
+  a.words = c->idx.words;
+  a.minor = L.minor;
+  a.blk_off = L.blk_off;
+  a.perm = L.perm;
+  a.items = cc.items;
+  a.n_items = cc.n_items;
+  a.col = cc.col;
+  a.smap = cc.smap;
+  a.rec = cc.rec;
+  a.c64 = cc.c64;
+  a.chi = cc.chi;
+  a.clo = cc.clo;
+  a.n_cls = cc.n_cls;
+  a.err = cc.err;
+}
+
+int build_layout(mcd_ctx* c, Layout& L, const LayoutItems& li, const std::vector<uint16_t>& bcls,
+                 const std::vector<double>& coef, double mem_budget, int64_t& bytes_out) {
+  ConnCache& cc = L.cc;
+  cudaStream_t s = c->stream;
+  const int64_t n_slices = li.n_slices;
+  cc.n_items = int64_t(li.items.size());
+  cc.n_slices = n_slices;
+  cc.max_stage = li.max_stage;
+  cc.n_cls = int(coef.size());
+  const int nc1 = std::max(cc.n_cls, 1);
+  cudaError_t e = grow(cc.items, cc.items_cap, cc.n_items, sizeof(CItem), s);
+  if (e == cudaSuccess) e = grow(cc.col, cc.col_cap, n_slices + 1 + 4, 4, s);   // + 16 bytes: whole-unit copies
+  if (e == cudaSuccess) e = grow(cc.smap, cc.smap_cap, n_slices * 32, 2, s);
+  // [c64: nc1 doubles][chi: nc1 floats][clo: nc1 floats][error word]
+  if (e == cudaSuccess) e = grow(cc.c64, cc.cls_cap, int64_t(nc1) * 2 + 1, 8, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cache: tables");
+  cc.chi = reinterpret_cast<float*>(cc.c64 + nc1);
+  cc.clo = cc.chi + nc1;
+  cc.err = reinterpret_cast<unsigned int*>(cc.clo + nc1);
+  std::vector<float> hi(coef.size()), lo(coef.size());
+  for (size_t i = 0; i < coef.size(); ++i) {
+    hi[i] = float(coef[i]);
+    lo[i] = float(coef[i] - double(hi[i]));
+  }
+  uint16_t* d_bcls = nullptr;
+  uint16_t* d_cnt = nullptr;
+  unsigned long long* d_nc = nullptr;
+  uint32_t* wid = nullptr;
+  auto release = [&] {
+    cudaFreeAsync(d_bcls, s);
+    cudaFreeAsync(d_cnt, s);
+    cudaFreeAsync(d_nc, s);
+    cudaFreeAsync(wid, s);
+  };
+  e = cudaMemcpyAsync(cc.items, li.items.data(), li.items.size() * sizeof(CItem), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !coef.empty()) {
+    e = cudaMemcpyAsync(cc.c64, coef.data(), coef.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cc.chi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cc.clo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(cc.err, 0, 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_bcls, std::max<size_t>(bcls.size(), 1) * 2, s);
+  if (e == cudaSuccess && !bcls.empty())
+    e = cudaMemcpyAsync(d_bcls, bcls.data(), bcls.size() * 2, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_cnt, size_t(std::max<int64_t>(L.n, 1)) * 2, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_nc, 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_nc, 0, 8, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&wid, size_t(n_slices + 1) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(wid + n_slices, 0, 4, s);
+  CArgs a;
+  fill_args(c, L, a);
+  a.bond_cls = d_bcls;
+  a.cnt = d_cnt;
+  a.wid = wid;
+  a.smap_out = cc.smap;
+  a.nconn = d_nc;
+  a.xs_cap = kBuildStageWords;
+  const int grid = int(std::min<int64_t>(cc.n_items, int64_t(sm_count(c->device)) * 8));
+  const int smem = kBuildStageWords * 4;
+  uint32_t total = 0;
+  unsigned long long nconn = 0;
+  if (e == cudaSuccess && cc.n_items > 0) {
+    cudaFuncSetAttribute(cache_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(cache_write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cache_count_kernel<<<grid, kCT, smem, s>>>(a, *c->hp);
+    MCD_LAUNCHED(c);
+    cache_sort_kernel<<<grid, kCT, 0, s>>>(a);
+    MCD_LAUNCHED(c);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = scan_u32(c, wid, cc.col, n_slices + 1, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, cc.col + n_slices, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nconn, d_nc, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  const int64_t bytes = int64_t(total) * kGroup;
+  if (e == cudaSuccess && double(bytes) > mem_budget) {
+    release();
+    cc.failed = 1;
+    return MCD_OK;
+  }
+  if (e == cudaSuccess) e = grow_bytes(cc.rec, cc.rec_cap, bytes, s);
+  a.rec = cc.rec;
+  if (e == cudaSuccess && cc.n_items > 0 && total > 0) {
+    cache_write_kernel<<<grid, kCT, smem, s>>>(a, *c->hp);
+    MCD_LAUNCHED(c);
+    e = cudaGetLastError();
+  }
+  release();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cc.valid = 0;
+    return cuda_fail(c, e, "cache build");
+  }
+  cc.n_groups = total;
+  cc.n_conn = int64_t(nconn);
+  cc.valid = 1;
+  bytes_out = bytes;
+  return MCD_OK;
+}
+
+// Records of both layouts for the current basis and Hamiltonian.
+int cache_build(mcd_ctx* c) {
+  const HamParams& hp = *c->hp;
+  // record classes: amplitude classes when there is a class table, else bonds
+  std::vector<uint16_t> bcls(size_t(hp.n_bonds));
+  std::vector<double> coef;
+  if (hp.n_class > 0) {
+    int b = 0;
+    for (int cl = 0; cl < hp.n_class; ++cl) {
+      for (; b < hp.cls_end[cl]; ++b) bcls[size_t(b)] = uint16_t(cl);
+      coef.push_back(hp.cls_t[cl]);
+    }
+  } else {
+    for (int b = 0; b < hp.n_bonds; ++b) {
+      bcls[size_t(b)] = uint16_t(b);
+      coef.push_back(hp.bonds[b].t);
+    }
+  }
+  Layout* Ls[2] = {&c->idx.B, &c->idx.A};
+  const bool wide_all = int(coef.size()) > Rec<uint16_t>::kMaxCls;
+  LayoutItems li[2];
+  int64_t max_stage = 0;
+  for (int i = 0; i < 2; ++i) {
+    Ls[i]->cc.valid = 0;
+    Ls[i]->cc.failed = 0;
+    std::vector<uint32_t> off(size_t(Ls[i]->nblk) + 1);
+    cudaError_t e = cudaMemcpyAsync(off.data(), Ls[i]->blk_off, off.size() * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cache: block offsets");
+    make_items(off, wide_all, li[i]);
+    max_stage = std::max(max_stage, li[i].max_stage);
+  }
+  if (int(coef.size()) > Rec<uint32_t>::kMaxCls || max_stage > int64_t(Rec<uint32_t>::kMaxStage)) {
+    for (Layout* L : Ls) L->cc.failed = 1;
+    return MCD_OK;
+  }
+  size_t freeb = 0, totb = 0;
+  cudaMemGetInfo(&freeb, &totb);
+  // auto: records of both passes within half the free memory
+  double budget = c->hv_cache == 2 ? double(freeb) : 0.5 * double(freeb);
+  int64_t nconn = 0;
+  for (int i = 0; i < 2; ++i) {
+    int64_t bytes = 0;
+    const int st = build_layout(c, *Ls[i], li[i], bcls, coef, budget, bytes);
+    if (st != MCD_OK) return st;
+    if (Ls[i]->cc.failed) {
+      for (Layout* L : Ls) {
+        L->cc.valid = 0;
+        L->cc.failed = 1;
+      }
+      return MCD_OK;
+    }
+    Ls[i]->cc.rec_bytes = wide_all ? 4 : 2;
+    budget -= double(bytes);
+    nconn += Ls[i]->cc.n_conn;
+  }
+  if (c->idx.A.cc.valid && c->idx.B.cc.valid) c->idx.nnz = nconn;
+  return MCD_OK;
+}
+
+int cls_bytes(mcd_ctx* c) {
+  int off = 0;
+  for (Layout* L : {&c->idx.B, &c->idx.A}) off = std::max(off, L->cc.n_cls * 16);
+  return (off + 127) & ~127;
+}
+
+template <typename T>
+cudaError_t launch_stream(mcd_ctx* c, const void* x, void* y, double* partials, int max_parts, unsigned int* ticket,
+                          double* dot_out) {
+  const int smem = kSStages * kSStageBytes + cls_bytes(c);
+  static int configured = -1;   // per instantiation
+  if (configured < smem) {
+    cudaFuncSetAttribute(hv_stream_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(hv_stream_kernel<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(hv_stream_kernel<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    configured = smem;
+  }
+  ConnCache& cb = c->idx.B.cc;
+  const int64_t n = c->idx.n;
+  // x in dn-major order for pass B and pass B's part of y (padded so that
+  // 16-byte copies stay inside)
+  const int64_t xb_bytes = (n * int64_t(sizeof(T)) + 15) & ~int64_t(15);
+  cudaError_t e = grow_bytes(cb.xb, cb.xb_cap, xb_bytes + 64, c->stream);
+  if (e == cudaSuccess) e = grow_bytes(cb.yb, cb.yb_cap, xb_bytes + 64, c->stream);
+  if (e != cudaSuccess) return e;
+  const int ctas = std::max(1, sm_count(c->device) * (smem <= 110 * 1024 ? 2 : 1));
+  for (int pass = 0; pass < 2; ++pass) {
+    const Layout& L = pass == 0 ? c->idx.B : c->idx.A;
+    CArgs a;
+    fill_args(c, L, a);
+    a.x = x;
+    a.y = y;
+    a.xb = cb.xb;
+    a.yb = cb.yb;
+    a.ncols = 1;
+    a.ld = 1;
+    // pass A reads the caller's x: only whole 16-byte units inside it
+    a.x_bytes = pass == 0 ? xb_bytes
+                          : ((reinterpret_cast<uintptr_t>(x) % 16 == 0) ? (n * int64_t(sizeof(T))) & ~int64_t(15) : 0);
+    const bool dot = pass == 1 && partials != nullptr;
+    a.dot_partials = partials;
+    a.ticket = ticket;
+    a.dot_out = dot_out;
+    int64_t grid = std::min<int64_t>(a.n_items, ctas);
+    if (dot) grid = std::min<int64_t>(grid, max_parts);
+    if (grid <= 0) {
+      if (!dot) continue;
+      grid = 1;   // an empty basis still writes <x, y> = 0
+    }
+    timing_begin(c, pass == 0 ? 0 : 1);
+    if (pass == 0) {
+      permute_kernel<T><<<int((n + 255) / 256), 256, 0, c->stream>>>(static_cast<const T*>(x), 1, L.perm, n,
+                                                                     static_cast<T*>(cb.xb));
+      MCD_LAUNCHED(c);
+      hv_stream_kernel<T, false, false><<<int(grid), kSThreads, smem, c->stream>>>(a, *c->hp);
+    } else if (dot) {
+      hv_stream_kernel<T, true, true><<<int(grid), kSThreads, smem, c->stream>>>(a, *c->hp);
+    } else {
+      hv_stream_kernel<T, true, false><<<int(grid), kSThreads, smem, c->stream>>>(a, *c->hp);
+    }
+    MCD_LAUNCHED(c);
+    timing_end(c);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T, int VEC, int G>
+cudaError_t launch_cached(mcd_ctx* c, const void* x, void* y, int ncols, int ld) {
+  const int chunks = (ncols + VEC - 1) / VEC;
+  const int ncp = chunks * VEC;
+  const int off_xs = cls_bytes(c);
+  const int smem = off_xs + kMStageBytes;
+  static int configured = -1;   // per instantiation
+  if (configured < smem) {
+    cudaFuncSetAttribute(hv_cached_kernel<T, VEC, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(hv_cached_kernel<T, VEC, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    configured = smem;
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    const Layout& L = pass == 0 ? c->idx.B : c->idx.A;
+    CArgs a;
+    fill_args(c, L, a);
+    a.x = x;
+    a.y = y;
+    a.ncols = ncols;
+    a.ld = ld;
+    a.ncp = ncp;
+    a.off_xs = off_xs;
+    a.xs_cap = int(kMStageBytes / sizeof(T));
+    if (a.n_items <= 0) continue;
+    timing_begin(c, pass == 0 ? 0 : 1);
+    if (pass == 0)
+      hv_cached_kernel<T, VEC, G, false><<<int(a.n_items), kCT, smem, c->stream>>>(a, *c->hp);
+    else
+      hv_cached_kernel<T, VEC, G, true><<<int(a.n_items), kCT, smem, c->stream>>>(a, *c->hp);
+    MCD_LAUNCHED(c);
+    timing_end(c);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T, int VEC>
+cudaError_t dispatch_cols(mcd_ctx* c, const void* x, void* y, int ncols, int ld, bool* used) {
+  const int chunks = (ncols + VEC - 1) / VEC;
+  *used = true;
+  if (chunks <= 1) return launch_cached<T, VEC, 1>(c, x, y, ncols, ld);
+  if (chunks <= 2) return launch_cached<T, VEC, 2>(c, x, y, ncols, ld);
+  if (chunks <= 4) return launch_cached<T, VEC, 4>(c, x, y, ncols, ld);
+  if (chunks <= 6) return launch_cached<T, VEC, 6>(c, x, y, ncols, ld);
+  if (chunks <= 8) return launch_cached<T, VEC, 8>(c, x, y, ncols, ld);
+  if (chunks <= 12) return launch_cached<T, VEC, 12>(c, x, y, ncols, ld);
+  if (chunks <= 16) return launch_cached<T, VEC, 16>(c, x, y, ncols, ld);
+  *used = false;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t dispatch(mcd_ctx* c, const void* x, void* y, int ncols, int ld, double* partials, int max_parts,
+                     unsigned int* ticket, double* dot_out, bool* used) {
+  if (ncols == 1 && ld == 1) {
+    *used = true;
+    return launch_stream<T>(c, x, y, partials, max_parts, ticket, dot_out);
+  }
+  if (partials) {   // the fused <x, y> is only formed for contiguous single columns
+    *used = false;
+    return cudaSuccess;
+  }
+  if (ncols == 1) {
+    *used = true;
+    return launch_cached<T, 1, 1>(c, x, y, ncols, ld);
+  }
+  constexpr int VEC = sizeof(T) == 4 ? 4 : 2;
+  const bool vec_ok = ld % VEC == 0 && reinterpret_cast<uintptr_t>(x) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(y) % 16 == 0;
+  if (!vec_ok) {
+    *used = false;
+    return cudaSuccess;
+  }
+  return dispatch_cols<T, VEC>(c, x, y, ncols, ld, used);
+}
+
+}  // namespace
+
+void cache_invalidate(Layout& L) {
+  L.cc.valid = 0;
+  L.cc.failed = 0;
+}
+
+void free_cache(Layout& L) {
+  ConnCache& cc = L.cc;
+  auto f = [](void* p) { if (p) cudaFree(p); };
+  f(cc.items); f(cc.col); f(cc.smap); f(cc.rec); f(cc.c64); f(cc.xb); f(cc.yb);
+  cc = ConnCache();
+}
+
+int cache_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, double* dot_partials,
+                int max_parts, unsigned int* ticket, double* dot_out, bool* used) {
+  *used = false;
+  ConnCache& A = c->idx.A.cc;
+  ConnCache& B = c->idx.B.cc;
+  if (!(A.valid && B.valid)) {
+    if (!(A.failed || B.failed)) {
+      const int st = cache_build(c);
+      if (st != MCD_OK) return st;
+    }
+    if (!(A.valid && B.valid)) {
+      if (c->hv_cache == 2) return fail(c, MCD_E_INVALID, "connection cache cannot be built for this basis");
+      return MCD_OK;
+    }
+  }
+  const cudaError_t e =
+      dtype == MCD_F64 ? dispatch<double>(c, x, y, ncols, ld, dot_partials, max_parts, ticket, dot_out, used)
+                       : dispatch<float>(c, x, y, ncols, ld, dot_partials, max_parts, ticket, dot_out, used);
+  return e == cudaSuccess ? MCD_OK : cuda_fail(c, e, "cached H*v launch");
+}
+
+int cache_errors(mcd_ctx* c, unsigned int* out) {
+  unsigned int v = 0, w = 0;
+  cudaError_t e = cudaSuccess;
+  if (c->idx.A.cc.err) e = cudaMemcpyAsync(&v, c->idx.A.cc.err, 4, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && c->idx.B.cc.err)
+    e = cudaMemcpyAsync(&w, c->idx.B.cc.err, 4, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cache error word");
+  *out = v | w;
+  return MCD_OK;
+}
+
+}  // namespace mcd

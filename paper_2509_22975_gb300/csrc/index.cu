@@ -235,6 +235,7 @@ static cudaError_t build_layout(mcd_ctx* c, const uint32_t* major, int64_t n, La
   L.nblk = int64_t(last_scan) + last_flag;
   L.n_items = (n + kItem - 1) / kItem;
   L.hash_built = 0;   // hash items describe the previous basis
+  cache_invalidate(L);
   block_tables_kernel<<<grid_of(n, T), T, 0, s>>>(major, tmp_flag, tmp_scan, n, L.blk_off,
                                                   L.blk_major, L.item_blk);
   MCD_LAUNCHED(c);
@@ -247,6 +248,7 @@ void free_index(DevIndex& ix) {
   for (Layout* L : {&ix.A, &ix.B}) {
     f(L->minor); f(L->blk_off); f(L->blk_major); f(L->item_blk); f(L->perm);
     free_hash(*L);
+    free_cache(*L);
     *L = Layout();
   }
   ix.words = nullptr;
@@ -260,14 +262,16 @@ static cudaError_t reserve_index(DevIndex& ix, int64_t n) {
   if (ix.cap >= n && ix.words) return cudaSuccess;
   free_index(ix);
   const int64_t items = (n + kItem - 1) / kItem + 1;
-  cudaError_t e = cudaMalloc(&ix.words, n * sizeof(uint64_t));
+  // words and perm end 16 bytes past the last state: the streaming H~v kernel
+  // copies aligned 16-byte units that cover a range of states
+  cudaError_t e = cudaMalloc(&ix.words, (n + 2) * sizeof(uint64_t));
   for (Layout* L : {&ix.A, &ix.B}) {
     if (e == cudaSuccess) e = cudaMalloc(&L->minor, n * 4);
     if (e == cudaSuccess) e = cudaMalloc(&L->blk_off, (n + 1) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&L->blk_major, n * 4);
     if (e == cudaSuccess) e = cudaMalloc(&L->item_blk, items * 4);
   }
-  if (e == cudaSuccess) e = cudaMalloc(&ix.B.perm, n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&ix.B.perm, (n + 4) * 4);
   if (e != cudaSuccess) {
     free_index(ix);
     return e;

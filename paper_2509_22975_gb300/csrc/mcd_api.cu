@@ -167,6 +167,14 @@ int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
       if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "SAMPLER_DEVICE must be 0, 1 or 2");
       c->sampler_where = int(value);
       return MCD_OK;
+    case MCD_OPT_HV_CACHE:
+      if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "HV_CACHE must be 0, 1 or 2");
+      c->hv_cache = int(value);
+      if (value == 1 && has_device(c)) {   // release the records
+        free_cache(c->idx.A);
+        free_cache(c->idx.B);
+      }
+      return MCD_OK;
     case MCD_OPT_SAMPLER_THREADS:
       if (value < 0 || value > 1024) return fail(c, MCD_E_INVALID, "SAMPLER_THREADS out of range");
       c->sampler_threads = int(value);
@@ -386,6 +394,8 @@ int mcd_set_hamiltonian(mcd_ctx* c, int n, const double* t, const double* eps, c
     }
   }
   c->has_ham = true;
+  cache_invalidate(c->idx.A);   // records hold classes and signs of this Hamiltonian's bonds
+  cache_invalidate(c->idx.B);
   if (sector_changed) {
     c->basis.clear();
     c->n_basis = 0;
@@ -517,6 +527,27 @@ int mcd_basis_info(mcd_ctx* c, int64_t* n_states, int64_t* n_up_blocks, int64_t*
       if (st != MCD_OK) return st;
     }
     *nnz = c->idx.nnz;
+  }
+  return MCD_OK;
+}
+
+int mcd_hv_cache_info(mcd_ctx* c, int64_t* bytes, int64_t* n_conn, int* rec_bytes, int* wait_errors) {
+  if (!c) return MCD_E_INVALID;
+  int st = need_basis(c);
+  if (st != MCD_OK) return st;
+  const ConnCache& A = c->idx.A.cc;
+  const ConnCache& B = c->idx.B.cc;
+  const bool ok = has_device(c) && A.valid && B.valid;
+  if (bytes) *bytes = ok ? (A.n_groups + B.n_groups) * 512 : 0;
+  if (n_conn) *n_conn = ok ? A.n_conn + B.n_conn : 0;
+  if (rec_bytes) *rec_bytes = ok ? A.rec_bytes : 0;
+  if (wait_errors) {
+    unsigned int v = 0;
+    if (ok) {
+      st = cache_errors(c, &v);
+      if (st != MCD_OK) return st;
+    }
+    *wait_errors = v ? 1 : 0;
   }
   return MCD_OK;
 }

@@ -92,6 +92,46 @@ constexpr uint32_t kHashSearch = 0xFFu;
 // One of the two orderings of the basis used by the H*v kernels.
 //   up-major (A): basis order; blocks share an up word; minor = dn word.
 //   dn-major (B): stable order by dn word; blocks share a dn word; minor = up.
+// Work item of the connection cache (hv_cache.cu): layout positions [lo, hi)
+// of the blocks b0..b1; every hop target of its states lies in the stage
+// range [blk_off[b0], blk_off[b1 + 1]), and a record holds the target's
+// position relative to blk_off[b0].  Its states, sorted by their number of
+// records (most first, ties in position order), form slices of 32, numbered
+// from slice0; flags bit 0 = 4-byte records.
+struct CItem {
+  uint32_t lo, hi, b0, b1, slice0, flags;
+};
+
+// Connection cache of one layout: the found hops of every state of the
+// pass, as records in slices of 32 states.  smap[32 s + l] is the state of
+// lane l of slice s (position relative to its item's lo; 0xFFFF = none).
+// Record group g (512 bytes) of a slice holds 16 bytes per lane: the next
+// 16 / record-size records of the lane's state, padded with all-ones
+// records.  col[s] is the first group of slice s (col[n_slices] = total).
+// Records: 2 bytes = pos:14 | sign:1 | class:1, or 4 bytes = pos:22 |
+// sign:1 | class:9; class indexes the coefficient tables (amplitude classes,
+// or bonds when there is no class table).
+struct ConnCache {
+  int valid = 0;                 // built for the current basis and Hamiltonian
+  int failed = 0;                // cannot be built for them (auto mode falls back)
+  int rec_bytes = 0;             // 2 (some items may hold 4-byte records) or 4 (all)
+  int n_cls = 0;
+  int64_t n_items = 0, n_slices = 0, n_groups = 0;
+  int64_t max_stage = 0;         // largest stage range of an item (states)
+  int64_t n_conn = 0;            // found hops (records that are not padding)
+  CItem* items = nullptr;
+  uint32_t* col = nullptr;       // [n_slices + 1]
+  uint16_t* smap = nullptr;      // [n_slices * 32]
+  void* rec = nullptr;           // [n_groups * 512 bytes]
+  double* c64 = nullptr;         // [n_cls] coefficient
+  float* chi = nullptr;          // [n_cls] coefficient split in two floats
+  float* clo = nullptr;
+  void* xb = nullptr;            // x in this layout's order (streaming kernel of pass B)
+  void* yb = nullptr;            // pass B's part of y (streaming kernels), read by pass A
+  unsigned int* err = nullptr;   // set by a kernel whose bounded wait ran out
+  int64_t items_cap = 0, col_cap = 0, smap_cap = 0, rec_cap = 0, cls_cap = 0, xb_cap = 0, yb_cap = 0;
+};
+
 struct Layout {
   int64_t n = 0;
   int64_t nblk = 0;
@@ -112,6 +152,7 @@ struct Layout {
   int64_t hflt_len = 0;          // 32-bit words
   int64_t hflt_cap = 0;
   uint32_t* hflt = nullptr;
+  ConnCache cc;                  // found hops of every state (hv_cache.cu)
 };
 
 struct DevIndex {
@@ -182,6 +223,7 @@ struct mcd_ctx {
   int timing = 0;
   int sampler_threads = 0;
   int sampler_where = 0;                // 0 auto, 1 host threads, 2 device
+  int hv_cache = 0;                     // 0 auto, 1 off, 2 required
   mcd::Timing* tm = nullptr;
 };
 
@@ -248,6 +290,16 @@ bool hash_eligible(const mcd_ctx* c);
 int hash_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, double* dot_partials,
                int max_parts, unsigned int* ticket, double* dot_out);
 void free_hash(Layout& L);
+
+// connection cache (hv_cache.cu): built by the first H*v of a basis (when
+// c->hv_cache allows and hv_algo == 0), then used by every H*v whose columns
+// it covers; returns MCD_OK and sets *used when it applied y = H~ x
+int cache_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, double* dot_partials,
+                int max_parts, unsigned int* ticket, double* dot_out, bool* used);
+void cache_invalidate(Layout& L);
+void free_cache(Layout& L);
+// *out = 1 when a bounded wait of a cached kernel gave up since the records were built
+int cache_errors(mcd_ctx* c, unsigned int* out);
 
 // Lanczos (krylov.cu)
 int lanczos_ground(mcd_ctx* c, int max_iter, double tol, uint64_t seed, int dtype,

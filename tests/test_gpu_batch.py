@@ -60,7 +60,9 @@ def test_batch_apply_equals_single_and_oracle(batch12, dtype):
     for i, (m, c) in enumerate(zip(ms, ctxs)):
         xi = x[off[i]:off[i + 1]].clone()
         yi = torch.empty_like(xi)
+        c.mcd_set_option(pkg.MCD_OPT_HV_CACHE, pkg.CACHE_OFF)   # the matrix-free kernel the batch shares
         c.mcd_apply(xi, yi)
+        c.mcd_set_option(pkg.MCD_OPT_HV_CACHE, pkg.CACHE_AUTO)
         torch.cuda.synchronize()
         assert torch.equal(yi, y[off[i]:off[i + 1]])          # same kernel arithmetic
         if i < 4:

@@ -110,11 +110,16 @@ def test_diagonal(which, request):
     assert np.array_equal(d.cpu().numpy(), P.diag)   # integer-valued here: exact
 
 
-# (algorithm, states per hash work item): the hash kernel at its default item
-# size (1024) and at 64 states per item, where most blocks are split into chunks
-# that share a table in device memory
-ALGOS = [(pkg.HV_AUTO, 1024), (pkg.HV_SEARCH, 1024), (pkg.HV_HASH, 1024), (pkg.HV_HASH, 64)]
-ALGO_IDS = ["auto", "search", "hash", "hash-item64"]
+# (algorithm, states per hash work item, connection cache): the cached path
+# (records built by the first H~x, then streamed), the matrix-free default
+# kernels (bitmap for <= 16 sites, hash above), the in-block binary search,
+# and the hash kernel at its default item size (1024) and at 64 states per
+# item, where most blocks are split into chunks that share a table in device
+# memory
+ALGOS = [(pkg.HV_AUTO, 1024, pkg.CACHE_REQUIRED), (pkg.HV_AUTO, 1024, pkg.CACHE_OFF),
+         (pkg.HV_SEARCH, 1024, pkg.CACHE_OFF), (pkg.HV_HASH, 1024, pkg.CACHE_OFF),
+         (pkg.HV_HASH, 64, pkg.CACHE_OFF)]
+ALGO_IDS = ["cached", "matrix-free", "search", "hash", "hash-item64"]
 
 
 @pytest.fixture(params=ALGOS, ids=ALGO_IDS)
@@ -123,9 +128,10 @@ def algo(request):
 
 
 def with_algo(ctx, algo):
-    a, item = algo
+    a, item = algo[:2]
     ctx.mcd_set_option(pkg.MCD_OPT_HV_ALGO, a)
     ctx.mcd_set_option(pkg.MCD_OPT_HASH_ITEM, item)
+    ctx.mcd_set_option(pkg.MCD_OPT_HV_CACHE, algo[2] if len(algo) > 2 else pkg.CACHE_AUTO)
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
