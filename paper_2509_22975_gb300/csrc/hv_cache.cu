@@ -55,8 +55,13 @@ constexpr int kBuildStageWords = 12288;      // minor words staged by the build 
 constexpr int kMStageBytes = 48 * 1024;      // staged x rows of the multi-column kernel
 constexpr int kMaxCount = 512;               // records of one state in one pass (n_bonds <= 496)
 // streaming one-column kernel
-constexpr int kSConsumers = 8;
-constexpr int kSThreads = 32 * (kSConsumers + 1);
+// consumer warps per CTA: 12 for fp32 vectors (72 registers, two CTAs per
+// SM), 8 for fp64 (the fp64 kernels need more registers per thread)
+template <typename T>
+struct SCfg {
+  static constexpr int kCons = sizeof(T) == 4 ? 12 : 8;
+  static constexpr int kThreads = 32 * (kCons + 1);
+};
 constexpr int kSStages = 2;
 constexpr int kSRecBytes = 24 * 1024;        // records of one item per stage
 constexpr int kSMapBytes = (kCItem / 32) * kSliceMap;
@@ -295,7 +300,21 @@ __global__ void __launch_bounds__(kCT) cache_write_kernel(const CArgs a, const H
   }
 }
 
+// g0, g1 of every item from the slice offsets
+__global__ void item_groups_kernel(CItem* items, int64_t n_items, const uint32_t* col) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_items) return;
+  CItem& it = items[i];
+  it.g0 = col[it.slice0];
+  it.g1 = col[it.slice0 + (it.hi - it.lo + 31) / 32];
+}
+
 // ---- apply --------------------------------------------------------------------------
+
+__device__ __forceinline__ float flip_sign(float x, uint32_t sg) { return __int_as_float(__float_as_int(x) ^ int(sg)); }
+__device__ __forceinline__ double flip_sign(double x, uint32_t sg) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (static_cast<long long>(sg) << 32));
+}
 
 template <typename T>
 __device__ __forceinline__ T coef_hi(const double* c64, const float* chi, int c) {
@@ -343,21 +362,30 @@ __device__ __forceinline__ void state_sum(const unsigned char* rp, int ng, int n
       if (r[0] == RR::kSent) continue;   // padding is trailing: the rest of the group is padding
       T xv[RR::kPer][VEC];
 #pragma unroll
-      for (int h = 0; h < RR::kPer; ++h)
-        if (r[h] != RR::kSent) gather(int(RR::pos(r[h])), xv[h]);
+      for (int h = 0; h < RR::kPer; ++h) {
+        if (r[h] != RR::kSent) {
+          gather(int(RR::pos(r[h])), xv[h]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) xv[h][u] = T(0);
+        }
+      }
 #pragma unroll
       for (int h = 0; h < RR::kPer; ++h) {
-        if (r[h] == RR::kSent) continue;
-        const bool ng_ = RR::neg(r[h]);
         if constexpr (sizeof(R) == 2) {
-          if (RR::cls(r[h])) {
+          // branch-free: the sign flips the sign bit of x (exact), the class
+          // picks the sum; padding adds a zero (exact)
+          const bool c1 = (r[h] >> 15) & 1u;
+          const uint32_t sg = (r[h] << 17) & 0x80000000u;
 #pragma unroll
-            for (int u = 0; u < VEC; ++u) s1[u] += ng_ ? -xv[h][u] : xv[h][u];
-          } else {
-#pragma unroll
-            for (int u = 0; u < VEC; ++u) s0[u] += ng_ ? -xv[h][u] : xv[h][u];
+          for (int u = 0; u < VEC; ++u) {
+            const T v = flip_sign(xv[h][u], sg);
+            s0[u] += c1 ? T(0) : v;
+            s1[u] += c1 ? v : T(0);
           }
         } else {
+          if (r[h] == RR::kSent) continue;
+          const bool ng_ = RR::neg(r[h]);
           const int cl = int(RR::cls(r[h]));
           if (cl != cur) {
             if (cur >= 0) {
@@ -482,6 +510,53 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
+// One item of the streaming kernel, for the calling consumer warp: its
+// slices warp, warp + SCfg<T>::kCons, ...  colp = slice offsets from the item's
+// first slice, recp = the item's first record group, mapp = lane map, xs =
+// x row of stage position 0, wp / pp / ybp = basis word, basis index and
+// pass B's part of y of the item's states (by position from it.lo).
+template <typename T, bool PASS_A, bool DOT>
+__device__ __forceinline__ void consume_item(const CArgs& a, const HamParams& hp, const CItem& it, uint32_t sb,
+                                             const uint32_t* colp, const unsigned char* recp, const uint16_t* mapp,
+                                             const T* xs, const uint64_t* wp, const uint32_t* pp, const T* ybp,
+                                             const double* c64, const float* chi, const float* clo,
+                                             const float* dhi, const float* dlo, const double* d64,
+                                             double& dot_acc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t half = a.n_sites >= 32 ? 0xFFFFFFFFu : ((1u << a.n_sites) - 1u);
+  const int nsl = int((it.hi - it.lo + 31) / 32);
+  const uint32_t g0 = colp[0];
+  const bool wide = (it.flags & 1u) != 0u;
+  T* __restrict__ y = static_cast<T*>(a.y);
+  T* __restrict__ yb = static_cast<T*>(a.yb);
+  for (int sl = warp; sl < nsl; sl += SCfg<T>::kCons) {
+    const uint16_t loc = mapp[sl * 32 + lane];
+    if (loc == kNoState) continue;
+    const uint32_t k = it.lo + loc;
+    const uint32_t ga = colp[sl], gz = colp[sl + 1];
+    const unsigned char* rp = recp + int64_t(ga - g0) * kGroup + lane * 16;
+    Acc<T> acc[1];
+    acc[0].zero();
+    auto gather = [&](int q, T* v) { v[0] = xs[q]; };
+    if (wide)
+      state_sum<T, uint32_t, 1, 4>(rp, int(gz - ga), a.n_cls, c64, chi, clo, gather, acc);
+    else
+      state_sum<T, uint16_t, 1, 4>(rp, int(gz - ga), a.n_cls, c64, chi, clo, gather, acc);
+    if (PASS_A) {
+      const uint64_t w = wp[loc];
+      const uint32_t up = uint32_t(w >> a.n_sites), dn = uint32_t(w) & half;
+      const T xk = xs[k - sb];
+      const Coef<T> dc = diag_of<T>(hp, dhi, dlo, d64, up, dn);
+      acc[0].fma(dc.hi, dc.lo, xk);
+      const T out = acc[0].value() + ybp[loc];
+      y[k] = out;
+      if constexpr (DOT) dot_acc += double(xk) * double(out);
+    } else {
+      yb[pp[loc]] = acc[0].value();
+    }
+  }
+}
+
 // One column, persistent and warp-specialised (see the top of the file).
 // Items of this CTA: blockIdx.x + i gridDim.x.  Stage i % kSStages holds
 // item i: its records, lane map, slice offsets, the x rows of its stage
@@ -489,19 +564,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // the basis index (pass B), each copied as whole aligned 16-byte units that
 // cover the range.  full[st] completes when the bytes have landed (or the
 // producer has marked the item direct: consumers then read global memory),
-// empty[st] when the kSConsumers consumer warps are done with it.
+// empty[st] when the SCfg<T>::kCons consumer warps are done with it.
 template <typename T, bool PASS_A, bool DOT>
-__global__ void __launch_bounds__(kSThreads, 2) hv_stream_kernel(const CArgs a, const HamParams hp) {
+__global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const CArgs a, const HamParams hp) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ __align__(8) uint64_t s_full[kSStages], s_empty[kSStages];
   __shared__ int s_direct[kSStages], s_xoff[kSStages], s_coff[kSStages], s_aoff[kSStages], s_boff[kSStages];
+  __shared__ CItem s_item[kSStages];
+  __shared__ uint32_t s_sb[kSStages];
   __shared__ float s_dhi[kMaxSites + 1], s_dlo[kMaxSites + 1];
   __shared__ double s_d64[kMaxSites + 1];
-  __shared__ double s_red[kSConsumers + 1];
+  __shared__ double s_red[SCfg<T>::kCons + 1];
   double* s_c64 = reinterpret_cast<double*>(s_dyn + kSStages * kSStageBytes);
   float* s_chi = reinterpret_cast<float*>(s_c64 + a.n_cls);
   float* s_clo = s_chi + a.n_cls;
-  for (int i = threadIdx.x; i < a.n_cls; i += kSThreads) {
+  for (int i = threadIdx.x; i < a.n_cls; i += SCfg<T>::kThreads) {
     s_c64[i] = a.c64[i];
     s_chi[i] = a.chi[i];
     s_clo[i] = a.clo[i];
@@ -514,7 +591,7 @@ __global__ void __launch_bounds__(kSThreads, 2) hv_stream_kernel(const CArgs a, 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kSStages; ++s) {
       mbar_init(&s_full[s], 1);
-      mbar_init(&s_empty[s], kSConsumers);
+      mbar_init(&s_empty[s], SCfg<T>::kCons);
     }
     mbar_fence_init();
   }
@@ -522,27 +599,29 @@ __global__ void __launch_bounds__(kSThreads, 2) hv_stream_kernel(const CArgs a, 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n_my = blockIdx.x < a.n_items ? (a.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const T* __restrict__ xg = static_cast<const T*>(PASS_A ? a.x : a.xb);   // rows in layout order
-  T* __restrict__ y = static_cast<T*>(a.y);
-  T* __restrict__ yb = static_cast<T*>(a.yb);                                // pass B's part of y
+  const T* __restrict__ yb = static_cast<const T*>(a.yb);                    // pass B's part of y
   const unsigned char* recg = static_cast<const unsigned char*>(a.rec);
   double dot_acc = 0.0;
   bool failed = false;
   int64_t issued[kSStages];   // producer: last item index issued into each stage (-1 none)
   for (int s = 0; s < kSStages; ++s) issued[s] = -1;
 
-  if (warp == kSConsumers) {
+  if (warp == SCfg<T>::kCons) {
     // producer: one thread issues the copies of the CTA's items, in order
     if (lane == 0) {
+      CItem nxt;   // descriptor of the next item, loaded while the current one is issued
+      if (n_my > 0) nxt = a.items[blockIdx.x];
       for (int64_t i = 0; i < n_my; ++i) {
         const int st = int(i % kSStages);
+        const CItem it = nxt;
+        if (i + 1 < n_my) nxt = a.items[blockIdx.x + (i + 1) * gridDim.x];
         if (!mbar_wait(&s_empty[st], uint32_t((i / kSStages) & 1) ^ 1u)) {
           failed = true;
           break;
         }
-        const CItem it = a.items[blockIdx.x + i * gridDim.x];
-        const uint32_t sb = a.blk_off[it.b0], se = a.blk_off[it.b1 + 1];
+        const uint32_t sb = it.sb, se = it.se;
         const int nsl = int((it.hi - it.lo + 31) / 32);
-        const uint32_t g0 = a.col[it.slice0], g1 = a.col[it.slice0 + nsl];
+        const uint32_t g0 = it.g0, g1 = it.g1;
         const uint32_t rb = (g1 - g0) * uint32_t(kGroup);
         const uint32_t mb = uint32_t(nsl) * kSliceMap;
         // 16-byte units covering [first, last) elements of size es
@@ -560,6 +639,8 @@ __global__ void __launch_bounds__(kSThreads, 2) hv_stream_kernel(const CArgs a, 
           span(it.lo, it.hi, 4, alo, ahi);            // basis index of each position
         }
         const bool direct = rb > uint32_t(kSRecBytes) || xhi - xlo > int64_t(kSXBytes) || xhi > a.x_bytes;
+        s_item[st] = it;
+        s_sb[st] = sb;
         s_direct[st] = direct ? 1 : 0;
         s_xoff[st] = int((int64_t(sb) * int64_t(sizeof(T)) - xlo) / int64_t(sizeof(T)));
         s_coff[st] = int((int64_t(it.slice0) * 4 - clo) / 4);
@@ -591,55 +672,28 @@ __global__ void __launch_bounds__(kSThreads, 2) hv_stream_kernel(const CArgs a, 
     }
   } else {
     // consumers
-    const uint32_t half = a.n_sites >= 32 ? 0xFFFFFFFFu : ((1u << a.n_sites) - 1u);
     for (int64_t i = 0; i < n_my; ++i) {
       const int st = int(i % kSStages);
       if (!mbar_wait(&s_full[st], uint32_t((i / kSStages) & 1))) {
         failed = true;
         break;
       }
-      const CItem it = a.items[blockIdx.x + i * gridDim.x];
-      const uint32_t sb = a.blk_off[it.b0];
-      const int nsl = int((it.hi - it.lo + 31) / 32);
-      const bool direct = s_direct[st] != 0;
+      const CItem it = s_item[st];
       const unsigned char* stage = s_dyn + st * kSStageBytes;
-      // per item: where each array of the item lives (stage, or global memory)
-      const uint32_t* colp = direct ? a.col + it.slice0
-                                    : reinterpret_cast<const uint32_t*>(stage + kSOffCol) + s_coff[st];
-      const uint32_t g0 = colp[0];
-      const unsigned char* recp = direct ? recg + int64_t(g0) * kGroup : stage;
-      const uint16_t* mapp =
-          direct ? a.smap + int64_t(it.slice0) * 32 : reinterpret_cast<const uint16_t*>(stage + kSOffMap);
-      const T* xs = direct ? xg + sb : reinterpret_cast<const T*>(stage + kSOffX) + s_xoff[st];
-      const uint64_t* wp = direct ? a.words + it.lo : reinterpret_cast<const uint64_t*>(stage + kSOffAux) + s_aoff[st];
-      const uint32_t* pp = direct ? a.perm + it.lo : reinterpret_cast<const uint32_t*>(stage + kSOffAux) + s_aoff[st];
-      const T* ybp = direct ? yb + it.lo : reinterpret_cast<const T*>(stage + kSOffAux2) + s_boff[st];
-      const bool wide = (it.flags & 1u) != 0u;
-      for (int sl = warp; sl < nsl; sl += kSConsumers) {
-        const uint16_t loc = mapp[sl * 32 + lane];
-        if (loc == kNoState) continue;
-        const uint32_t k = it.lo + loc;
-        const uint32_t ga = colp[sl], gz = colp[sl + 1];
-        const unsigned char* rp = recp + int64_t(ga - g0) * kGroup + lane * 16;
-        Acc<T> acc[1];
-        acc[0].zero();
-        auto gather = [&](int q, T* v) { v[0] = xs[q]; };
-        if (wide)
-          state_sum<T, uint32_t, 1, 4>(rp, int(gz - ga), a.n_cls, s_c64, s_chi, s_clo, gather, acc);
-        else
-          state_sum<T, uint16_t, 1, 4>(rp, int(gz - ga), a.n_cls, s_c64, s_chi, s_clo, gather, acc);
-        if (PASS_A) {
-          const uint64_t w = wp[loc];
-          const uint32_t up = uint32_t(w >> a.n_sites), dn = uint32_t(w) & half;
-          const T xk = xs[k - sb];
-          const Coef<T> dc = diag_of<T>(hp, s_dhi, s_dlo, s_d64, up, dn);
-          acc[0].fma(dc.hi, dc.lo, xk);
-          const T out = acc[0].value() + ybp[loc];
-          y[k] = out;
-          if constexpr (DOT) dot_acc += double(xk) * double(out);
-        } else {
-          yb[pp[loc]] = acc[0].value();
-        }
+      if (s_direct[st] == 0) {   // every array of the item in the stage: shared-memory loads
+        const uint32_t* colp = reinterpret_cast<const uint32_t*>(stage + kSOffCol) + s_coff[st];
+        consume_item<T, PASS_A, DOT>(a, hp, it, s_sb[st], colp, stage,
+                                     reinterpret_cast<const uint16_t*>(stage + kSOffMap),
+                                     reinterpret_cast<const T*>(stage + kSOffX) + s_xoff[st],
+                                     reinterpret_cast<const uint64_t*>(stage + kSOffAux) + s_aoff[st],
+                                     reinterpret_cast<const uint32_t*>(stage + kSOffAux) + s_aoff[st],
+                                     reinterpret_cast<const T*>(stage + kSOffAux2) + s_boff[st], s_c64, s_chi,
+                                     s_clo, s_dhi, s_dlo, s_d64, dot_acc);
+      } else {                   // too large for the stage: global memory
+        const uint32_t sb = s_sb[st];
+        consume_item<T, PASS_A, DOT>(a, hp, it, sb, a.col + it.slice0, recg + int64_t(it.g0) * kGroup,
+                                     a.smap + int64_t(it.slice0) * 32, xg + sb, a.words + it.lo, a.perm + it.lo,
+                                     yb + it.lo, s_c64, s_chi, s_clo, s_dhi, s_dlo, s_d64, dot_acc);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&s_empty[st]);
@@ -647,7 +701,7 @@ __global__ void __launch_bounds__(kSThreads, 2) hv_stream_kernel(const CArgs a, 
   }
   const int any_failed = __syncthreads_or(failed ? 1 : 0);
   if (any_failed) {
-    if (warp == kSConsumers && lane == 0) {
+    if (warp == SCfg<T>::kCons && lane == 0) {
       // copies still in flight land before the CTA's shared memory is released
       for (int s = 0; s < kSStages; ++s)
         if (issued[s] >= 0) mbar_wait(&s_full[s], uint32_t((issued[s] / kSStages) & 1));
@@ -655,7 +709,7 @@ __global__ void __launch_bounds__(kSThreads, 2) hv_stream_kernel(const CArgs a, 
     if (threadIdx.x == 0) atomicOr(a.err, 1u);
     __syncthreads();
   }
-  if constexpr (DOT) dot_reduce<kSConsumers + 1>(a, dot_acc, s_red);
+  if constexpr (DOT) dot_reduce<SCfg<T>::kCons + 1>(a, dot_acc, s_red);
 }
 
 // x in the layout's order: xb[k] = x[perm[k]] (one column, stride ld)
@@ -731,10 +785,12 @@ __global__ void __launch_bounds__(kCT) hv_cached_kernel(const CArgs a, const Ham
     for (int sl = warp; sl < nsl; sl += kCWarps) {
       const int64_t s = int64_t(it.slice0) + sl;
       const uint32_t ga = __ldg(a.col + s), gz = __ldg(a.col + s + 1);
-      if (!lane_ok || cvalid <= 0) continue;   // lanes past the last column chunk idle
-      for (int t = tg; t < 32; t += kSPW) {
-        const uint16_t loc = __ldg(a.smap + s * 32 + t);
-        if (loc == kNoState) break;            // empty lanes are the slice's last ones
+      const uint32_t locs = __ldg(a.smap + s * 32 + lane);   // the slice's lane map, one load per warp
+      for (int t0 = 0; t0 < 32; t0 += kSPW) {
+        const int t = t0 + tg;
+        const uint16_t loc = uint16_t(__shfl_sync(0xffffffffu, locs, t & 31));
+        if (!lane_ok || cvalid <= 0 || t >= 32) continue;   // idle lanes: past the last column chunk
+        if (loc == kNoState) continue;                      // empty lanes are the slice's last ones
         const uint32_t k = it.lo + loc;
         const unsigned char* rp = recg + int64_t(ga) * kGroup + t * 16;
         Acc<T> acc[VEC];
@@ -821,7 +877,7 @@ void make_items(const std::vector<uint32_t>& off, bool wide_all, LayoutItems& li
   auto add = [&](uint32_t lo, uint32_t hi, uint32_t b0, uint32_t b1) {
     const int64_t stage = int64_t(off[b1 + 1]) - off[b0];
     const bool wide = wide_all || stage > int64_t(Rec<uint16_t>::kMaxStage);
-    li.items.push_back(CItem{lo, hi, b0, b1, uint32_t(li.n_slices), wide ? 1u : 0u});
+    li.items.push_back(CItem{lo, hi, b0, b1, uint32_t(li.n_slices), wide ? 1u : 0u, off[b0], off[b1 + 1], 0u, 0u});
     li.n_slices += (hi - lo + 31) / 32;
     li.max_stage = std::max(li.max_stage, stage);
   };
@@ -946,6 +1002,11 @@ int build_layout(mcd_ctx* c, Layout& L, const LayoutItems& li, const std::vector
   a.rec = cc.rec;
   if (e == cudaSuccess && cc.n_items > 0 && total > 0) {
     cache_write_kernel<<<grid, kCT, smem, s>>>(a, *c->hp);
+    MCD_LAUNCHED(c);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && cc.n_items > 0) {
+    item_groups_kernel<<<int((cc.n_items + 255) / 256), 256, 0, s>>>(cc.items, cc.n_items, cc.col);
     MCD_LAUNCHED(c);
     e = cudaGetLastError();
   }
@@ -1076,11 +1137,11 @@ cudaError_t launch_stream(mcd_ctx* c, const void* x, void* y, double* partials, 
       permute_kernel<T><<<int((n + 255) / 256), 256, 0, c->stream>>>(static_cast<const T*>(x), 1, L.perm, n,
                                                                      static_cast<T*>(cb.xb));
       MCD_LAUNCHED(c);
-      hv_stream_kernel<T, false, false><<<int(grid), kSThreads, smem, c->stream>>>(a, *c->hp);
+      hv_stream_kernel<T, false, false><<<int(grid), SCfg<T>::kThreads, smem, c->stream>>>(a, *c->hp);
     } else if (dot) {
-      hv_stream_kernel<T, true, true><<<int(grid), kSThreads, smem, c->stream>>>(a, *c->hp);
+      hv_stream_kernel<T, true, true><<<int(grid), SCfg<T>::kThreads, smem, c->stream>>>(a, *c->hp);
     } else {
-      hv_stream_kernel<T, true, false><<<int(grid), kSThreads, smem, c->stream>>>(a, *c->hp);
+      hv_stream_kernel<T, true, false><<<int(grid), SCfg<T>::kThreads, smem, c->stream>>>(a, *c->hp);
     }
     MCD_LAUNCHED(c);
     timing_end(c);

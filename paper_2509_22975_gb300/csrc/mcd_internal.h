@@ -97,9 +97,10 @@ constexpr uint32_t kHashSearch = 0xFFu;
 // range [blk_off[b0], blk_off[b1 + 1]), and a record holds the target's
 // position relative to blk_off[b0].  Its states, sorted by their number of
 // records (most first, ties in position order), form slices of 32, numbered
-// from slice0; flags bit 0 = 4-byte records.
+// from slice0; flags bit 0 = 4-byte records.  sb, se = its stage range,
+// g0, g1 = its record groups [g0, g1) (filled once the records are laid out).
 struct CItem {
-  uint32_t lo, hi, b0, b1, slice0, flags;
+  uint32_t lo, hi, b0, b1, slice0, flags, sb, se, g0, g1;
 };
 
 // Connection cache of one layout: the found hops of every state of the
