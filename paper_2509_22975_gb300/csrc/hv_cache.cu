@@ -300,6 +300,109 @@ __global__ void __launch_bounds__(kCT) cache_write_kernel(const CArgs a, const H
   }
 }
 
+// Builds for n_sites <= 16: the in-block lookup by a shared bitmap of the
+// block's minor words (bit per word value, with the stage position of the
+// first set bit of each 32-bit word), block by block; same bond order, so
+// the same records as the binary-search build.
+template <typename F>
+__device__ __forceinline__ uint32_t enumerate_bm(const HamParams& hp, const uint2* bm, uint32_t m, F f) {
+  uint32_t cnt = 0;
+  for (int bi = 0; bi < hp.n_bonds; ++bi) {
+    const uint32_t mk = hp.bonds[bi].mask;
+    if (__popc(m & mk) != 1) continue;
+    const uint32_t m2 = m ^ mk;
+    const uint2 w = bm[m2 >> 5];
+    const uint32_t sh = m2 & 31u;
+    if (!((w.x >> sh) & 1u)) continue;
+    f(cnt, w.y + __popc(w.x & ((1u << sh) - 1u)), __popc(m & hp.bonds[bi].between) & 1u, bi);
+    ++cnt;
+  }
+  return cnt;
+}
+
+template <typename R>
+__device__ __forceinline__ void write_bm(const CArgs& a, const HamParams& hp, const uint16_t* s_cls, const uint2* bm,
+                                        const CItem& it, uint32_t m, int slot) {
+  constexpr int kRow = kGroup / int(sizeof(R));
+  const int64_t s = int64_t(it.slice0) + slot / 32;
+  const uint32_t g0 = a.col[s];
+  const int width = int(a.col[s + 1] - g0) * Rec<R>::kPer;
+  R* base = static_cast<R*>(a.rec) + int64_t(g0) * kRow + (slot % 32) * Rec<R>::kPer;
+  auto put = [&](uint32_t j, uint32_t r) {
+    if (int(j) < width) base[int64_t(j / Rec<R>::kPer) * kRow + (j % Rec<R>::kPer)] = R(r);
+  };
+  const uint32_t cnt = enumerate_bm(hp, bm, m, [&](uint32_t j, uint32_t q, uint32_t ng, int bi) {
+    put(j, Rec<R>::make(q, ng, s_cls[bi]));
+  });
+  for (int j = int(cnt); j < width; ++j) put(uint32_t(j), Rec<R>::kSent);
+}
+
+// WRITE = false: cnt[k] and nconn; WRITE = true: the records (the slots of
+// an item's states from the inverse of its lane map; padding of empty slots
+// by the lanes that own them)
+template <bool WRITE>
+__global__ void __launch_bounds__(kCT) cache_bm_kernel(const CArgs a, const HamParams hp, int nw) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  uint2* bm = reinterpret_cast<uint2*>(s_dyn);   // [nw]
+  __shared__ uint16_t s_cls[kMaxBonds];
+  __shared__ uint16_t s_slot[kCItem];
+  for (int i = threadIdx.x; i < nw; i += kCT) bm[i] = make_uint2(0u, 0u);
+  for (int i = threadIdx.x; i < hp.n_bonds; i += kCT) s_cls[i] = a.bond_cls[i];
+  unsigned long long nc = 0;
+  for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const CItem it = a.items[item];
+    const uint32_t sb = it.sb;
+    const int nsl = int((it.hi - it.lo + 31) / 32);
+    const bool wide = (it.flags & 1u) != 0u;
+    __syncthreads();
+    if (WRITE) {
+      for (int p = threadIdx.x; p < nsl * 32; p += kCT) {
+        const uint16_t loc = a.smap[int64_t(it.slice0) * 32 + p];
+        if (loc != kNoState) {
+          s_slot[loc] = uint16_t(p);
+        } else {   // an empty slot: its lane's records are all padding
+          const int64_t s = int64_t(it.slice0) + p / 32;
+          const uint32_t g0 = a.col[s], g1 = a.col[s + 1];
+          for (uint32_t g = g0; g < g1; ++g)
+            *reinterpret_cast<uint4*>(static_cast<unsigned char*>(a.rec) + int64_t(g) * kGroup + (p % 32) * 16) =
+                make_uint4(~0u, ~0u, ~0u, ~0u);
+        }
+      }
+    }
+    for (uint32_t b = it.b0; b <= it.b1; ++b) {
+      const uint32_t bs = a.blk_off[b], be = a.blk_off[b + 1];
+      __syncthreads();
+      for (uint32_t q = threadIdx.x; q < be - bs; q += kCT) {
+        const uint32_t d = a.minor[bs + q];
+        atomicOr(&bm[d >> 5].x, 1u << (d & 31));
+        if (q == 0 || (a.minor[bs + q - 1] >> 5) != (d >> 5)) bm[d >> 5].y = bs - sb + q;
+      }
+      __syncthreads();
+      const uint32_t klo = bs > it.lo ? bs : it.lo, khi = be < it.hi ? be : it.hi;
+      for (uint32_t k = klo + threadIdx.x; k < khi; k += kCT) {
+        const uint32_t m = a.minor[k];
+        if (WRITE) {
+          if (wide)
+            write_bm<uint32_t>(a, hp, s_cls, bm, it, m, s_slot[k - it.lo]);
+          else
+            write_bm<uint16_t>(a, hp, s_cls, bm, it, m, s_slot[k - it.lo]);
+        } else {
+          const uint32_t c = enumerate_bm(hp, bm, m, [](uint32_t, uint32_t, uint32_t, int) {});
+          a.cnt[k] = uint16_t(c);
+          nc += c;
+        }
+      }
+      __syncthreads();
+      for (uint32_t q = threadIdx.x; q < be - bs; q += kCT) bm[a.minor[bs + q] >> 5].x = 0u;
+    }
+  }
+  if (!WRITE) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nc += __shfl_xor_sync(0xffffffffu, nc, o);
+    if ((threadIdx.x & 31) == 0 && nc) atomicAdd(a.nconn, nc);
+  }
+}
+
 // g0, g1 of every item from the slice offsets
 __global__ void item_groups_kernel(CItem* items, int64_t n_items, const uint32_t* col) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -979,10 +1082,18 @@ int build_layout(mcd_ctx* c, Layout& L, const LayoutItems& li, const std::vector
   const int smem = kBuildStageWords * 4;
   uint32_t total = 0;
   unsigned long long nconn = 0;
+  // n_sites <= 16: bitmap lookups (2^n bits of the block's minor words as
+  // (bits, first position) pairs); above: binary search in the staged words
+  const bool bitmap = c->n <= 16;
+  const int nw = c->n >= 5 ? (1 << (c->n - 5)) : 1;
+  const int smem_bm = nw * 8;
   if (e == cudaSuccess && cc.n_items > 0) {
     cudaFuncSetAttribute(cache_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(cache_write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cache_count_kernel<<<grid, kCT, smem, s>>>(a, *c->hp);
+    if (bitmap)
+      cache_bm_kernel<false><<<grid, kCT, smem_bm, s>>>(a, *c->hp, nw);
+    else
+      cache_count_kernel<<<grid, kCT, smem, s>>>(a, *c->hp);
     MCD_LAUNCHED(c);
     cache_sort_kernel<<<grid, kCT, 0, s>>>(a);
     MCD_LAUNCHED(c);
@@ -1001,7 +1112,10 @@ int build_layout(mcd_ctx* c, Layout& L, const LayoutItems& li, const std::vector
   if (e == cudaSuccess) e = grow_bytes(cc.rec, cc.rec_cap, bytes, s);
   a.rec = cc.rec;
   if (e == cudaSuccess && cc.n_items > 0 && total > 0) {
-    cache_write_kernel<<<grid, kCT, smem, s>>>(a, *c->hp);
+    if (bitmap)
+      cache_bm_kernel<true><<<grid, kCT, smem_bm, s>>>(a, *c->hp, nw);
+    else
+      cache_write_kernel<<<grid, kCT, smem, s>>>(a, *c->hp);
     MCD_LAUNCHED(c);
     e = cudaGetLastError();
   }
