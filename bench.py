@@ -191,7 +191,7 @@ def traffic_for(kernel_key: str):
     if not ent:
         return None
     h = hashlib.sha256()
-    for f in ("hv_cache.cu", "hv_common.cuh"):
+    for f in ("hv_cache.cu", "hv_cache.cuh", "hv_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2509_22975_gb300", "csrc", f), "rb").read())
     return ent["bytes_per_launch"] if ent.get("kernel_src_sha") == h.hexdigest()[:16] else None
 
@@ -318,6 +318,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--hv-cols", type=int, nargs="*", default=[1, 24])
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-impurity batch measurement")
+    ap.add_argument("--no-hv-cache", action="store_true",
+                    help="matrix-free H*v kernels (no connection records) on the 4x4 workload")
     ap.add_argument("--no-rect24", action="store_true",
                     help="skip the 6x4 t-t' (24-site, 5e7-state) H*V measurements")
     args = ap.parse_args()
@@ -340,6 +342,8 @@ def main():
     w = configs.square16_u8()
     ctx = pkg.Context(local)
     ctx.mcd_set_hamiltonian(w.lat.t, w.eps, w.U, w.n_up, w.n_dn)
+    if args.no_hv_cache:
+        ctx.mcd_set_option(pkg.MCD_OPT_HV_CACHE, pkg.CACHE_OFF)
     t0 = time.perf_counter()
     ctx.mcd_build_basis(w.seed, args.n_f, w.beta, [w.seed_word()])
     t_sample = time.perf_counter() - t0
@@ -396,12 +400,15 @@ def main():
     alg_bytes = n * (8 + 2 * 1 * 4)
     peak, peak_src = measured_peak()
     achieved = alg_bytes / ((tA + tB) * 1e-3) / 1e9
-    tb, ta = traffic_for("hv_cached_pass_B_square16_fp32_L1"), traffic_for("hv_cached_pass_A_square16_fp32_L1")
+    tb, ta = (None, None) if args.no_hv_cache else (traffic_for("hv_cached_pass_B_square16_fp32_L1"),
+                                                      traffic_for("hv_cached_pass_A_square16_fp32_L1"))
     cinfo = ctx.mcd_hv_cache_info()
     rec_bytes = cinfo["bytes"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tb + ta) if (tb is not None and ta is not None) else None,
-                "kernel": "H~v pair (hv_cached_kernel pass B + pass A, records of the found hops), one application",
+                "kernel": ("H~v pair (matrix-free hv_l1_kernel pass B + pass A), one application" if args.no_hv_cache else
+                           "H~v pair (hv_stream_kernel pass B with its x permutation + pass A), records of the found "
+                           "hops, one application"),
                 "algorithmic_bytes": alg_bytes, "peak_source": peak_src,
                 "record_bytes": rec_bytes,
                 "achieved_incl_records": (alg_bytes + rec_bytes) / ((tA + tB) * 1e-3) / 1e9,
@@ -427,7 +434,7 @@ def main():
 
     # the record build alone: a fresh basis, first H~v minus the next one
     ctx.mcd_set_basis_device(words_dev)
-    build_ms = cache_build_ms(pkg, ctx, n, dev)
+    build_ms = None if args.no_hv_cache else cache_build_ms(pkg, ctx, n, dev)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

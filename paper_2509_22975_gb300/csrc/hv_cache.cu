@@ -40,23 +40,13 @@
 #include <algorithm>
 #include <vector>
 
-#include "hv_common.cuh"
+#include "hv_cache.cuh"
 
 namespace mcd {
 namespace {
 
-constexpr int kCT = 256;                     // threads of the build and multi-column kernels
-constexpr int kCWarps = kCT / 32;
-constexpr int kCItem = 512;                  // states per work item (at most, unless one block is larger)
-constexpr int kGroup = 512;                  // bytes of one record group: 32 lanes x 16 bytes
-constexpr int kSliceMap = 64;                // bytes of a slice's lane map (32 x u16)
-constexpr uint16_t kNoState = 0xFFFFu;
-constexpr int kBuildStageWords = 12288;      // minor words staged by the build kernels (48 KiB)
-constexpr int kMStageBytes = 48 * 1024;      // staged x rows of the multi-column kernel
-constexpr int kMaxCount = 512;               // records of one state in one pass (n_bonds <= 496)
-// streaming one-column kernel
-// consumer warps per CTA: 12 for fp32 vectors (72 registers, two CTAs per
-// SM), 8 for fp64 (the fp64 kernels need more registers per thread)
+// streaming one-column kernel: two CTAs per SM, each a producer warp and 12
+// (fp32 vectors) or 8 (fp64) consumer warps, two stages
 template <typename T>
 struct SCfg {
   static constexpr int kCons = sizeof(T) == 4 ? 12 : 8;
@@ -78,72 +68,6 @@ constexpr int kSStageBytes = kSOffAux2 + kSAux2Bytes;
 static_assert(kSStageBytes % 16 == 0 && kSOffX % 16 == 0 && kSOffAux % 16 == 0 && kSOffAux2 % 16 == 0,
               "stage buffers on 16-byte boundaries");
 constexpr uint32_t kSpinLimit = 1u << 22;    // polls of an mbarrier before a wait gives up
-
-template <typename R>
-struct Rec;
-template <>
-struct Rec<uint16_t> {
-  static constexpr int kPer = 8;                 // records per lane per group
-  static constexpr uint32_t kSent = 0xFFFFu;     // padding
-  static constexpr uint32_t kMaxStage = 0x3FFFu; // positions 0 .. 0x3FFE (0x3FFF + sign + class 1 = padding)
-  static constexpr int kMaxCls = 2;
-  __host__ __device__ static uint32_t make(uint32_t q, uint32_t neg, uint32_t cls) {
-    return q | (neg << 14) | (cls << 15);
-  }
-  __device__ static uint32_t pos(uint32_t r) { return r & 0x3FFFu; }
-  __device__ static bool neg(uint32_t r) { return (r >> 14) & 1u; }
-  __device__ static uint32_t cls(uint32_t r) { return r >> 15; }
-};
-template <>
-struct Rec<uint32_t> {
-  static constexpr int kPer = 4;
-  static constexpr uint32_t kSent = 0xFFFFFFFFu;
-  static constexpr uint32_t kMaxStage = 0x3FFFFFu;
-  static constexpr int kMaxCls = 512;
-  __host__ __device__ static uint32_t make(uint32_t q, uint32_t neg, uint32_t cls) {
-    return q | (neg << 22) | (cls << 23);
-  }
-  __device__ static uint32_t pos(uint32_t r) { return r & 0x3FFFFFu; }
-  __device__ static bool neg(uint32_t r) { return (r >> 22) & 1u; }
-  __device__ static uint32_t cls(uint32_t r) { return r >> 23; }
-};
-
-struct CArgs {
-  const void* x;
-  void* y;
-  const void* xb;                // pass B of the streaming kernel: x in layout order
-  void* yb;                      // streaming kernels: pass B's part of y (basis order), read by pass A
-  int ncols, ld;
-  int ncp;                       // staged row stride (elements)
-  int xs_cap;                    // staged elements (multi-column) / minor words (build)
-  int off_xs;                    // byte offset of the staging area in dynamic shared memory
-  int n_sites;
-  int64_t n;                     // states
-  int64_t x_bytes;               // bytes of x the streaming kernel may read from its base
-  const uint64_t* words;         // basis words (diagonal of pass A)
-  const uint32_t* minor;
-  const uint32_t* blk_off;
-  const uint32_t* perm;          // pass B: layout position -> basis index
-  const CItem* items;
-  int64_t n_items;
-  const uint32_t* col;           // [n_slices + 1] first record group of each slice
-  const uint16_t* smap;          // [n_slices * 32] lane -> state of the item
-  void* rec;
-  const double* c64;             // [n_cls]
-  const float* chi;
-  const float* clo;
-  int n_cls;
-  double* dot_partials;
-  unsigned int* ticket;
-  double* dot_out;
-  unsigned int* err;
-  // build
-  const uint16_t* bond_cls;      // [n_bonds] record class of each bond
-  uint16_t* cnt;                 // [n] records of each state
-  uint32_t* wid;                 // [n_slices] groups of each slice
-  uint16_t* smap_out;
-  unsigned long long* nconn;     // found hops
-};
 
 // ---- build ------------------------------------------------------------------------
 
@@ -414,163 +338,6 @@ __global__ void item_groups_kernel(CItem* items, int64_t n_items, const uint32_t
 
 // ---- apply --------------------------------------------------------------------------
 
-__device__ __forceinline__ float flip_sign(float x, uint32_t sg) { return __int_as_float(__float_as_int(x) ^ int(sg)); }
-__device__ __forceinline__ double flip_sign(double x, uint32_t sg) {
-  return __longlong_as_double(__double_as_longlong(x) ^ (static_cast<long long>(sg) << 32));
-}
-
-template <typename T>
-__device__ __forceinline__ T coef_hi(const double* c64, const float* chi, int c) {
-  return sizeof(T) == 4 ? T(chi[c]) : T(c64[c]);
-}
-template <typename T>
-__device__ __forceinline__ T coef_lo(const float* clo, int c) {
-  return sizeof(T) == 4 ? T(clo[c]) : T(0);
-}
-
-// acc += sum over the records of one state of t_class sign x[target] (VEC
-// columns).  rp = the lane's 16 bytes in the state's first group (shared or
-// global memory); ng groups, 512 bytes apart.  gather(q, v) loads the VEC
-// values of stage row q.  kU groups are loaded before any is used.
-template <typename T, typename R, int VEC, int kU, typename Gather>
-__device__ __forceinline__ void state_sum(const unsigned char* rp, int ng, int n_cls, const double* c64,
-                                          const float* chi, const float* clo, Gather gather, Acc<T> (&acc)[VEC]) {
-  using RR = Rec<R>;
-  T s0[VEC], s1[VEC];
-#pragma unroll
-  for (int u = 0; u < VEC; ++u) s0[u] = s1[u] = T(0);
-  int cur = -1;   // class of the running sum (4-byte records)
-  for (int gb = 0; gb < ng; gb += kU, rp += kU * kGroup) {
-    uint4 pks[kU];
-#pragma unroll
-    for (int v = 0; v < kU; ++v)
-      pks[v] = gb + v < ng ? *reinterpret_cast<const uint4*>(rp + v * kGroup) : make_uint4(~0u, ~0u, ~0u, ~0u);
-#pragma unroll
-    for (int v = 0; v < kU; ++v) {
-      const uint4 pk = pks[v];
-      uint32_t r[RR::kPer];
-      if constexpr (sizeof(R) == 2) {
-        const uint32_t w[4] = {pk.x, pk.y, pk.z, pk.w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          r[2 * h] = w[h] & 0xFFFFu;
-          r[2 * h + 1] = w[h] >> 16;
-        }
-      } else {
-        r[0] = pk.x;
-        r[1] = pk.y;
-        r[2] = pk.z;
-        r[3] = pk.w;
-      }
-      if (r[0] == RR::kSent) continue;   // padding is trailing: the rest of the group is padding
-      T xv[RR::kPer][VEC];
-#pragma unroll
-      for (int h = 0; h < RR::kPer; ++h) {
-        if (r[h] != RR::kSent) {
-          gather(int(RR::pos(r[h])), xv[h]);
-        } else {
-#pragma unroll
-          for (int u = 0; u < VEC; ++u) xv[h][u] = T(0);
-        }
-      }
-#pragma unroll
-      for (int h = 0; h < RR::kPer; ++h) {
-        if constexpr (sizeof(R) == 2) {
-          // branch-free: the sign flips the sign bit of x (exact), the class
-          // picks the sum; padding adds a zero (exact)
-          const bool c1 = (r[h] >> 15) & 1u;
-          const uint32_t sg = (r[h] << 17) & 0x80000000u;
-#pragma unroll
-          for (int u = 0; u < VEC; ++u) {
-            const T v = flip_sign(xv[h][u], sg);
-            s0[u] += c1 ? T(0) : v;
-            s1[u] += c1 ? v : T(0);
-          }
-        } else {
-          if (r[h] == RR::kSent) continue;
-          const bool ng_ = RR::neg(r[h]);
-          const int cl = int(RR::cls(r[h]));
-          if (cl != cur) {
-            if (cur >= 0) {
-              const T ch = coef_hi<T>(c64, chi, cur), cl_ = coef_lo<T>(clo, cur);
-#pragma unroll
-              for (int u = 0; u < VEC; ++u) {
-                acc[u].fma(ch, cl_, s0[u]);
-                s0[u] = T(0);
-              }
-            }
-            cur = cl;
-          }
-#pragma unroll
-          for (int u = 0; u < VEC; ++u) s0[u] += ng_ ? -xv[h][u] : xv[h][u];
-        }
-      }
-    }
-  }
-  if constexpr (sizeof(R) == 2) {
-    if (n_cls > 0) {
-      const T ch = coef_hi<T>(c64, chi, 0), cl_ = coef_lo<T>(clo, 0);
-#pragma unroll
-      for (int u = 0; u < VEC; ++u) acc[u].fma(ch, cl_, s0[u]);
-    }
-    if (n_cls > 1) {
-      const T ch = coef_hi<T>(c64, chi, 1), cl_ = coef_lo<T>(clo, 1);
-#pragma unroll
-      for (int u = 0; u < VEC; ++u) acc[u].fma(ch, cl_, s1[u]);
-    }
-  } else if (cur >= 0) {
-    const T ch = coef_hi<T>(c64, chi, cur), cl_ = coef_lo<T>(clo, cur);
-#pragma unroll
-    for (int u = 0; u < VEC; ++u) acc[u].fma(ch, cl_, s0[u]);
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ Coef<T> diag_of(const HamParams& hp, const float* dhi, const float* dlo,
-                                           const double* d64, uint32_t up, uint32_t dn) {
-  if (hp.uniform) {
-    const int nu = __popc(up & dn);
-    return Coef<T>{sizeof(T) == 4 ? T(dhi[nu]) : T(d64[nu]), sizeof(T) == 4 ? T(dlo[nu]) : T(0)};
-  }
-  return diag_coef<T>(hp, up, dn);
-}
-
-// Fixed-order <x, y> of pass A: CTA partials, then the last CTA sums them.
-template <int kWarps>
-__device__ __forceinline__ void dot_reduce(const CArgs& a, double dot_acc, double* s_red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) dot_acc += __shfl_xor_sync(0xffffffffu, dot_acc, o);
-  __syncthreads();
-  if (lane == 0) s_red[warp] = dot_acc;
-  __syncthreads();
-  __shared__ bool s_last;
-  if (threadIdx.x == 0) {
-    double sum = 0.0;
-    for (int w = 0; w < kWarps; ++w) sum += s_red[w];
-    a.dot_partials[blockIdx.x] = sum;
-    __threadfence();
-    const unsigned tk = atomicAdd(a.ticket, 1u);
-    s_last = (tk == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (s_last) {
-    double sum = 0.0;
-    for (int i = threadIdx.x; i < int(gridDim.x); i += blockDim.x) sum += __ldcg(a.dot_partials + i);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    __syncthreads();
-    if (lane == 0) s_red[warp] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < kWarps; ++w) tot += s_red[w];
-      *a.dot_out = tot;
-      *a.ticket = 0u;
-    }
-  }
-}
-
 // ---- mbarrier and bulk copy (PTX) -----------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -614,17 +381,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 // One item of the streaming kernel, for the calling consumer warp: its
-// slices warp, warp + SCfg<T>::kCons, ...  colp = slice offsets from the item's
-// first slice, recp = the item's first record group, mapp = lane map, xs =
-// x row of stage position 0, wp / pp / ybp = basis word, basis index and
-// pass B's part of y of the item's states (by position from it.lo).
+// slices warp, warp + kCons, ...  colp = slice offsets from the item's first
+// slice, recp = the item's first record group, mapp = lane map, xs = x row
+// of stage position 0, wp / pp / ybp = basis word, basis index and pass B's
+// part of y of the item's states (by position from it.lo).  DOT: the
+// thread's part of <x, y> as an unevaluated sum dh + dl (fp32 vectors: the
+// exact products summed with compensation, since GB300's fp64 pipe is too
+// narrow for a per-state fp64 product).
 template <typename T, bool PASS_A, bool DOT>
 __device__ __forceinline__ void consume_item(const CArgs& a, const HamParams& hp, const CItem& it, uint32_t sb,
                                              const uint32_t* colp, const unsigned char* recp, const uint16_t* mapp,
                                              const T* xs, const uint64_t* wp, const uint32_t* pp, const T* ybp,
                                              const double* c64, const float* chi, const float* clo,
-                                             const float* dhi, const float* dlo, const double* d64,
-                                             double& dot_acc) {
+                                             const float* dhi, const float* dlo, const double* d64, T& dh, T& dl) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t half = a.n_sites >= 32 ? 0xFFFFFFFFu : ((1u << a.n_sites) - 1u);
   const int nsl = int((it.hi - it.lo + 31) / 32);
@@ -653,9 +422,55 @@ __device__ __forceinline__ void consume_item(const CArgs& a, const HamParams& hp
       acc[0].fma(dc.hi, dc.lo, xk);
       const T out = acc[0].value() + ybp[loc];
       y[k] = out;
-      if constexpr (DOT) dot_acc += double(xk) * double(out);
+      if constexpr (DOT) {
+        if constexpr (sizeof(T) == 4) {
+          const T p = xk * out;
+          const T pe = fmaf(xk, out, -p);           // exact error of the product
+          const T ssum = dh + p, bb = ssum - dh;    // two-sum of the running hi part and p
+          dl += (dh - (ssum - bb)) + (p - bb) + pe;
+          dh = ssum;
+        } else {
+          dh = fma(xk, out, dh);
+        }
+      }
     } else {
       yb[pp[loc]] = acc[0].value();
+    }
+  }
+}
+
+// Fixed-order <x, y> of pass A: CTA partials, then the last CTA sums them.
+template <int kWarps>
+__device__ __forceinline__ void dot_reduce(const CArgs& a, double dot_acc, double* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dot_acc += __shfl_xor_sync(0xffffffffu, dot_acc, o);
+  __syncthreads();
+  if (lane == 0) s_red[warp] = dot_acc;
+  __syncthreads();
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < kWarps; ++w) sum += s_red[w];
+    a.dot_partials[blockIdx.x] = sum;
+    __threadfence();
+    const unsigned tk = atomicAdd(a.ticket, 1u);
+    s_last = (tk == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    double sum = 0.0;
+    for (int i = threadIdx.x; i < int(gridDim.x); i += blockDim.x) sum += __ldcg(a.dot_partials + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    __syncthreads();
+    if (lane == 0) s_red[warp] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < kWarps; ++w) tot += s_red[w];
+      *a.dot_out = tot;
+      *a.ticket = 0u;
     }
   }
 }
@@ -704,7 +519,7 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
   const T* __restrict__ xg = static_cast<const T*>(PASS_A ? a.x : a.xb);   // rows in layout order
   const T* __restrict__ yb = static_cast<const T*>(a.yb);                    // pass B's part of y
   const unsigned char* recg = static_cast<const unsigned char*>(a.rec);
-  double dot_acc = 0.0;
+  T dh = T(0), dl = T(0);   // this thread's part of <x, y> (consumers)
   bool failed = false;
   int64_t issued[kSStages];   // producer: last item index issued into each stage (-1 none)
   for (int s = 0; s < kSStages; ++s) issued[s] = -1;
@@ -791,12 +606,12 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
                                      reinterpret_cast<const uint64_t*>(stage + kSOffAux) + s_aoff[st],
                                      reinterpret_cast<const uint32_t*>(stage + kSOffAux) + s_aoff[st],
                                      reinterpret_cast<const T*>(stage + kSOffAux2) + s_boff[st], s_c64, s_chi,
-                                     s_clo, s_dhi, s_dlo, s_d64, dot_acc);
+                                     s_clo, s_dhi, s_dlo, s_d64, dh, dl);
       } else {                   // too large for the stage: global memory
         const uint32_t sb = s_sb[st];
         consume_item<T, PASS_A, DOT>(a, hp, it, sb, a.col + it.slice0, recg + int64_t(it.g0) * kGroup,
                                      a.smap + int64_t(it.slice0) * 32, xg + sb, a.words + it.lo, a.perm + it.lo,
-                                     yb + it.lo, s_c64, s_chi, s_clo, s_dhi, s_dlo, s_d64, dot_acc);
+                                     yb + it.lo, s_c64, s_chi, s_clo, s_dhi, s_dlo, s_d64, dh, dl);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&s_empty[st]);
@@ -812,7 +627,7 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
     if (threadIdx.x == 0) atomicOr(a.err, 1u);
     __syncthreads();
   }
-  if constexpr (DOT) dot_reduce<SCfg<T>::kCons + 1>(a, dot_acc, s_red);
+  if constexpr (DOT) dot_reduce<SCfg<T>::kCons + 1>(a, double(dh) + double(dl), s_red);
 }
 
 // x in the layout's order: xb[k] = x[perm[k]] (one column, stride ld)
@@ -821,115 +636,6 @@ __global__ void permute_kernel(const T* __restrict__ x, int ld, const uint32_t* 
                                T* __restrict__ xb) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k < n) xb[k] = x[int64_t(perm[k]) * ld];
-}
-
-// Many columns (or one column with a row stride): CTA per item, x rows of the
-// stage range staged with ordinary loads when they fit, G lanes per state.
-template <typename T, int VEC, int G, bool PASS_A>
-__global__ void __launch_bounds__(kCT) hv_cached_kernel(const CArgs a, const HamParams hp) {
-  extern __shared__ __align__(16) unsigned char s_dyn[];
-  double* s_c64 = reinterpret_cast<double*>(s_dyn);
-  float* s_chi = reinterpret_cast<float*>(s_c64 + a.n_cls);
-  float* s_clo = s_chi + a.n_cls;
-  T* xs = reinterpret_cast<T*>(s_dyn + a.off_xs);
-  __shared__ float s_dhi[kMaxSites + 1], s_dlo[kMaxSites + 1];
-  __shared__ double s_d64[kMaxSites + 1];
-  for (int i = threadIdx.x; i < a.n_cls; i += kCT) {
-    s_c64[i] = a.c64[i];
-    s_chi[i] = a.chi[i];
-    s_clo[i] = a.clo[i];
-  }
-  if (threadIdx.x <= kMaxSites) {
-    s_dhi[threadIdx.x] = hp.dtab_hi[threadIdx.x];
-    s_dlo[threadIdx.x] = hp.dtab_lo[threadIdx.x];
-    s_d64[threadIdx.x] = hp.dtab[threadIdx.x];
-  }
-  using C = ChunkOf<T, VEC>;
-  constexpr int kSPW = 32 / G;                   // states of a slice processed at once by a warp
-  constexpr int kU = VEC == 1 ? 4 : 1;           // record groups in flight per lane
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane % G, tg = lane / G;
-  const bool lane_ok = tg < kSPW;                // G not dividing 32 leaves lanes idle
-  const int col0 = g * VEC;
-  const int cvalid = a.ncols - col0;
-  const T* __restrict__ x = static_cast<const T*>(a.x);
-  T* __restrict__ y = static_cast<T*>(a.y);
-  const unsigned char* recg = static_cast<const unsigned char*>(a.rec);
-  const uint32_t half = a.n_sites >= 32 ? 0xFFFFFFFFu : ((1u << a.n_sites) - 1u);
-  const int ld = a.ld, ncp = a.ncp;
-
-  for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-    const CItem it = a.items[item];
-    const uint32_t sb = a.blk_off[it.b0], se = a.blk_off[it.b1 + 1];
-    const int nst = int(se - sb);
-    const bool staged = int64_t(nst) * ncp <= a.xs_cap;
-    __syncthreads();   // the previous item's rows are no longer read
-    if (staged && lane_ok && cvalid > 0) {
-      for (int q = warp * kSPW + tg; q < nst; q += kCWarps * kSPW) {
-        const int64_t row = PASS_A ? int64_t(sb) + q : int64_t(__ldg(a.perm + sb + q));
-        T v[VEC];
-        C::load(x + row * ld + col0, cvalid, v);
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) xs[q * ncp + col0 + u] = v[u];
-      }
-    }
-    __syncthreads();
-    const bool wide = (it.flags & 1u) != 0u;
-    auto gather = [&](int q, T* v) {
-      if (staged) {
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) v[u] = xs[q * ncp + col0 + u];
-      } else {
-        const int64_t row = PASS_A ? int64_t(sb) + q : int64_t(__ldg(a.perm + sb + q));
-        C::load(x + row * ld + col0, cvalid, v);
-      }
-    };
-    const int nsl = int((it.hi - it.lo + 31) / 32);
-    for (int sl = warp; sl < nsl; sl += kCWarps) {
-      const int64_t s = int64_t(it.slice0) + sl;
-      const uint32_t ga = __ldg(a.col + s), gz = __ldg(a.col + s + 1);
-      const uint32_t locs = __ldg(a.smap + s * 32 + lane);   // the slice's lane map, one load per warp
-      for (int t0 = 0; t0 < 32; t0 += kSPW) {
-        const int t = t0 + tg;
-        const uint16_t loc = uint16_t(__shfl_sync(0xffffffffu, locs, t & 31));
-        if (!lane_ok || cvalid <= 0 || t >= 32) continue;   // idle lanes: past the last column chunk
-        if (loc == kNoState) continue;                      // empty lanes are the slice's last ones
-        const uint32_t k = it.lo + loc;
-        const unsigned char* rp = recg + int64_t(ga) * kGroup + t * 16;
-        Acc<T> acc[VEC];
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) acc[u].zero();
-        if (wide)
-          state_sum<T, uint32_t, VEC, kU>(rp, int(gz - ga), a.n_cls, s_c64, s_chi, s_clo, gather, acc);
-        else
-          state_sum<T, uint16_t, VEC, kU>(rp, int(gz - ga), a.n_cls, s_c64, s_chi, s_clo, gather, acc);
-        T out[VEC];
-        if (PASS_A) {
-          const uint64_t w = __ldg(a.words + k);
-          const uint32_t up = uint32_t(w >> a.n_sites), dn = uint32_t(w) & half;
-          T xk[VEC], yk[VEC];
-          if (staged) {
-#pragma unroll
-            for (int u = 0; u < VEC; ++u) xk[u] = xs[int(k - sb) * ncp + col0 + u];
-          } else {
-            C::load(x + int64_t(k) * ld + col0, cvalid, xk);
-          }
-          C::load(y + int64_t(k) * ld + col0, cvalid, yk);
-          const Coef<T> dc = diag_of<T>(hp, s_dhi, s_dlo, s_d64, up, dn);
-#pragma unroll
-          for (int u = 0; u < VEC; ++u) {
-            acc[u].fma(dc.hi, dc.lo, xk[u]);
-            out[u] = acc[u].value() + yk[u];
-          }
-          C::store(y + int64_t(k) * ld + col0, cvalid, out);
-        } else {
-#pragma unroll
-          for (int u = 0; u < VEC; ++u) out[u] = acc[u].value();
-          C::store(y + int64_t(__ldg(a.perm + k)) * ld + col0, cvalid, out);
-        }
-      }
-    }
-  }
 }
 
 // ---- host ------------------------------------------------------------------------
@@ -1000,26 +706,6 @@ void make_items(const std::vector<uint32_t>& off, bool wide_all, LayoutItems& li
   }
 }
 
-void fill_args(mcd_ctx* c, const Layout& L, CArgs& a) {
-  const ConnCache& cc = L.cc;
-  a = CArgs{};
-  a.n_sites = c->n;
-  a.n = L.n;
-  a.words = c->idx.words;
-  a.minor = L.minor;
-  a.blk_off = L.blk_off;
-  a.perm = L.perm;
-  a.items = cc.items;
-  a.n_items = cc.n_items;
-  a.col = cc.col;
-  a.smap = cc.smap;
-  a.rec = cc.rec;
-  a.c64 = cc.c64;
-  a.chi = cc.chi;
-  a.clo = cc.clo;
-  a.n_cls = cc.n_cls;
-  a.err = cc.err;
-}
 
 int build_layout(mcd_ctx* c, Layout& L, const LayoutItems& li, const std::vector<uint16_t>& bcls,
                  const std::vector<double>& coef, double mem_budget, int64_t& bytes_out) {
@@ -1197,11 +883,6 @@ int cache_build(mcd_ctx* c) {
   return MCD_OK;
 }
 
-int cls_bytes(mcd_ctx* c) {
-  int off = 0;
-  for (Layout* L : {&c->idx.B, &c->idx.A}) off = std::max(off, L->cc.n_cls * 16);
-  return (off + 127) & ~127;
-}
 
 template <typename T>
 cudaError_t launch_stream(mcd_ctx* c, const void* x, void* y, double* partials, int max_parts, unsigned int* ticket,
@@ -1265,57 +946,6 @@ cudaError_t launch_stream(mcd_ctx* c, const void* x, void* y, double* partials, 
   return cudaSuccess;
 }
 
-template <typename T, int VEC, int G>
-cudaError_t launch_cached(mcd_ctx* c, const void* x, void* y, int ncols, int ld) {
-  const int chunks = (ncols + VEC - 1) / VEC;
-  const int ncp = chunks * VEC;
-  const int off_xs = cls_bytes(c);
-  const int smem = off_xs + kMStageBytes;
-  static int configured = -1;   // per instantiation
-  if (configured < smem) {
-    cudaFuncSetAttribute(hv_cached_kernel<T, VEC, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(hv_cached_kernel<T, VEC, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    configured = smem;
-  }
-  for (int pass = 0; pass < 2; ++pass) {
-    const Layout& L = pass == 0 ? c->idx.B : c->idx.A;
-    CArgs a;
-    fill_args(c, L, a);
-    a.x = x;
-    a.y = y;
-    a.ncols = ncols;
-    a.ld = ld;
-    a.ncp = ncp;
-    a.off_xs = off_xs;
-    a.xs_cap = int(kMStageBytes / sizeof(T));
-    if (a.n_items <= 0) continue;
-    timing_begin(c, pass == 0 ? 0 : 1);
-    if (pass == 0)
-      hv_cached_kernel<T, VEC, G, false><<<int(a.n_items), kCT, smem, c->stream>>>(a, *c->hp);
-    else
-      hv_cached_kernel<T, VEC, G, true><<<int(a.n_items), kCT, smem, c->stream>>>(a, *c->hp);
-    MCD_LAUNCHED(c);
-    timing_end(c);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
-template <typename T, int VEC>
-cudaError_t dispatch_cols(mcd_ctx* c, const void* x, void* y, int ncols, int ld, bool* used) {
-  const int chunks = (ncols + VEC - 1) / VEC;
-  *used = true;
-  if (chunks <= 1) return launch_cached<T, VEC, 1>(c, x, y, ncols, ld);
-  if (chunks <= 2) return launch_cached<T, VEC, 2>(c, x, y, ncols, ld);
-  if (chunks <= 4) return launch_cached<T, VEC, 4>(c, x, y, ncols, ld);
-  if (chunks <= 6) return launch_cached<T, VEC, 6>(c, x, y, ncols, ld);
-  if (chunks <= 8) return launch_cached<T, VEC, 8>(c, x, y, ncols, ld);
-  if (chunks <= 12) return launch_cached<T, VEC, 12>(c, x, y, ncols, ld);
-  if (chunks <= 16) return launch_cached<T, VEC, 16>(c, x, y, ncols, ld);
-  *used = false;
-  return cudaSuccess;
-}
 
 template <typename T>
 cudaError_t dispatch(mcd_ctx* c, const void* x, void* y, int ncols, int ld, double* partials, int max_parts,
@@ -1328,18 +958,7 @@ cudaError_t dispatch(mcd_ctx* c, const void* x, void* y, int ncols, int ld, doub
     *used = false;
     return cudaSuccess;
   }
-  if (ncols == 1) {
-    *used = true;
-    return launch_cached<T, 1, 1>(c, x, y, ncols, ld);
-  }
-  constexpr int VEC = sizeof(T) == 4 ? 4 : 2;
-  const bool vec_ok = ld % VEC == 0 && reinterpret_cast<uintptr_t>(x) % 16 == 0 &&
-                      reinterpret_cast<uintptr_t>(y) % 16 == 0;
-  if (!vec_ok) {
-    *used = false;
-    return cudaSuccess;
-  }
-  return dispatch_cols<T, VEC>(c, x, y, ncols, ld, used);
+  return cache_apply_cols(c, x, y, ncols, ld, sizeof(T) == 8 ? MCD_F64 : MCD_F32, used);
 }
 
 }  // namespace

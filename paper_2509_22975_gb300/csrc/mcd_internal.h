@@ -301,6 +301,9 @@ void cache_invalidate(Layout& L);
 void free_cache(Layout& L);
 // *out = 1 when a bounded wait of a cached kernel gave up since the records were built
 int cache_errors(mcd_ctx* c, unsigned int* out);
+// cached H*V for many columns, or one column with a row stride (hv_cache_cols.cu);
+// *used = false when the columns' layout is not covered (the caller falls back)
+cudaError_t cache_apply_cols(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, bool* used);
 
 // Lanczos (krylov.cu)
 int lanczos_ground(mcd_ctx* c, int max_iter, double tol, uint64_t seed, int dtype,
