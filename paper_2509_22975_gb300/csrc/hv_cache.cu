@@ -18,7 +18,7 @@
 // Layout of the records: the states of a work item are sorted by their
 // number of records (most first; equal counts in position order) and form
 // slices of 32; group g of a slice holds, for each lane l, the records
-// 8g..8g+7 (2-byte) or 4g..4g+3 (4-byte) of the lane's state, all ones past
+// 4g..4g+3 (2-byte) or 2g, 2g+1 (4-byte) of the lane's state, all ones past
 // its last record.  A slice has as many groups as its longest list needs
 // (sliced ELL with sorting inside the item), so one warp reads one slice
 // with every load aligned, little padding and no per-state offsets.
@@ -288,8 +288,8 @@ __global__ void __launch_bounds__(kCT) cache_bm_kernel(const CArgs a, const HamP
           const int64_t s = int64_t(it.slice0) + p / 32;
           const uint32_t g0 = a.col[s], g1 = a.col[s + 1];
           for (uint32_t g = g0; g < g1; ++g)
-            *reinterpret_cast<uint4*>(static_cast<unsigned char*>(a.rec) + int64_t(g) * kGroup + (p % 32) * 16) =
-                make_uint4(~0u, ~0u, ~0u, ~0u);
+            *reinterpret_cast<uint2*>(static_cast<unsigned char*>(a.rec) + int64_t(g) * kGroup + (p % 32) * kLaneBytes) =
+                make_uint2(~0u, ~0u);
         }
       }
     }
@@ -406,7 +406,7 @@ __device__ __forceinline__ void consume_item(const CArgs& a, const HamParams& hp
     if (loc == kNoState) continue;
     const uint32_t k = it.lo + loc;
     const uint32_t ga = colp[sl], gz = colp[sl + 1];
-    const unsigned char* rp = recp + int64_t(ga - g0) * kGroup + lane * 16;
+    const unsigned char* rp = recp + int64_t(ga - g0) * kGroup + lane * kLaneBytes;
     Acc<T> acc[1];
     acc[0].zero();
     auto gather = [&](int q, T* v) { v[0] = xs[q]; };

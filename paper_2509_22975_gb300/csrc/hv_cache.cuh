@@ -11,7 +11,8 @@ namespace {
 constexpr int kCT = 256;                     // threads of the build and multi-column kernels
 constexpr int kCWarps = kCT / 32;
 constexpr int kCItem = 512;                  // states per work item (at most, unless one block is larger)
-constexpr int kGroup = 512;                  // bytes of one record group: 32 lanes x 16 bytes
+constexpr int kLaneBytes = 8;                // bytes of a lane's records in one group
+constexpr int kGroup = 32 * kLaneBytes;      // bytes of one record group (256)
 constexpr int kSliceMap = 64;                // bytes of a slice's lane map (32 x u16)
 constexpr uint16_t kNoState = 0xFFFFu;
 constexpr int kBuildStageWords = 12288;      // minor words staged by the build kernels (48 KiB)
@@ -22,7 +23,7 @@ template <typename R>
 struct Rec;
 template <>
 struct Rec<uint16_t> {
-  static constexpr int kPer = 8;                 // records per lane per group
+  static constexpr int kPer = kLaneBytes / 2;   // records per lane per group
   static constexpr uint32_t kSent = 0xFFFFu;     // padding
   static constexpr uint32_t kMaxStage = 0x3FFFu; // positions 0 .. 0x3FFE (0x3FFF + sign + class 1 = padding)
   static constexpr int kMaxCls = 2;
@@ -35,7 +36,7 @@ struct Rec<uint16_t> {
 };
 template <>
 struct Rec<uint32_t> {
-  static constexpr int kPer = 4;
+  static constexpr int kPer = kLaneBytes / 4;
   static constexpr uint32_t kSent = 0xFFFFFFFFu;
   static constexpr uint32_t kMaxStage = 0x3FFFFFu;
   static constexpr int kMaxCls = 512;
@@ -101,8 +102,8 @@ __device__ __forceinline__ T coef_lo(const float* clo, int c) {
 }
 
 // acc += sum over the records of one state of t_class sign x[target] (VEC
-// columns).  rp = the lane's 16 bytes in the state's first group (shared or
-// global memory); ng groups, 512 bytes apart.  gather(q, v) loads the VEC
+// columns).  rp = the lane's 8 bytes in the state's first group (shared or
+// global memory); ng groups, 256 bytes apart.  gather(q, v) loads the VEC
 // values of stage row q.  kU groups are loaded before any is used.
 template <typename T, typename R, int VEC, int kU, typename Gather>
 __device__ __forceinline__ void state_sum(const unsigned char* rp, int ng, int n_cls, const double* c64,
@@ -113,26 +114,22 @@ __device__ __forceinline__ void state_sum(const unsigned char* rp, int ng, int n
   for (int u = 0; u < VEC; ++u) s0[u] = s1[u] = T(0);
   int cur = -1;   // class of the running sum (4-byte records)
   for (int gb = 0; gb < ng; gb += kU, rp += kU * kGroup) {
-    uint4 pks[kU];
+    uint2 pks[kU];
 #pragma unroll
     for (int v = 0; v < kU; ++v)
-      pks[v] = gb + v < ng ? *reinterpret_cast<const uint4*>(rp + v * kGroup) : make_uint4(~0u, ~0u, ~0u, ~0u);
+      pks[v] = gb + v < ng ? *reinterpret_cast<const uint2*>(rp + v * kGroup) : make_uint2(~0u, ~0u);
 #pragma unroll
     for (int v = 0; v < kU; ++v) {
-      const uint4 pk = pks[v];
+      const uint2 pk = pks[v];
       uint32_t r[RR::kPer];
       if constexpr (sizeof(R) == 2) {
-        const uint32_t w[4] = {pk.x, pk.y, pk.z, pk.w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          r[2 * h] = w[h] & 0xFFFFu;
-          r[2 * h + 1] = w[h] >> 16;
-        }
+        r[0] = pk.x & 0xFFFFu;
+        r[1] = pk.x >> 16;
+        r[2] = pk.y & 0xFFFFu;
+        r[3] = pk.y >> 16;
       } else {
         r[0] = pk.x;
         r[1] = pk.y;
-        r[2] = pk.z;
-        r[3] = pk.w;
       }
       if (r[0] == RR::kSent) continue;   // padding is trailing: the rest of the group is padding
       T xv[RR::kPer][VEC];

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kCT) hv_cached_kernel(const CArgs a, const Ham
   }
   using C = ChunkOf<T, VEC>;
   constexpr int kSPW = 32 / G;                   // states of a slice processed at once by a warp
-  constexpr int kU = VEC == 1 ? 4 : 1;           // record groups in flight per lane
+  constexpr int kU = VEC == 1 ? 8 : 2;           // record groups in flight per lane
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane % G, tg = lane / G;
   const bool lane_ok = tg < kSPW;                // G not dividing 32 leaves lanes idle
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kCT) hv_cached_kernel(const CArgs a, const Ham
         if (!lane_ok || cvalid <= 0 || t >= 32) continue;   // idle lanes: past the last column chunk
         if (loc == kNoState) continue;                      // empty lanes are the slice's last ones
         const uint32_t k = it.lo + loc;
-        const unsigned char* rp = recg + int64_t(ga) * kGroup + t * 16;
+        const unsigned char* rp = recg + int64_t(ga) * kGroup + t * kLaneBytes;
         Acc<T> acc[VEC];
 #pragma unroll
         for (int u = 0; u < VEC; ++u) acc[u].zero();

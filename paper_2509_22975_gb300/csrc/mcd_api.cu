@@ -538,7 +538,7 @@ int mcd_hv_cache_info(mcd_ctx* c, int64_t* bytes, int64_t* n_conn, int* rec_byte
   const ConnCache& A = c->idx.A.cc;
   const ConnCache& B = c->idx.B.cc;
   const bool ok = has_device(c) && A.valid && B.valid;
-  if (bytes) *bytes = ok ? (A.n_groups + B.n_groups) * 512 : 0;
+  if (bytes) *bytes = ok ? (A.n_groups + B.n_groups) * 256 : 0;
   if (n_conn) *n_conn = ok ? A.n_conn + B.n_conn : 0;
   if (rec_bytes) *rec_bytes = ok ? A.rec_bytes : 0;
   if (wait_errors) {

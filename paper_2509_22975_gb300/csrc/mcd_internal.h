@@ -106,7 +106,7 @@ struct CItem {
 // Connection cache of one layout: the found hops of every state of the
 // pass, as records in slices of 32 states.  smap[32 s + l] is the state of
 // lane l of slice s (position relative to its item's lo; 0xFFFF = none).
-// Record group g (512 bytes) of a slice holds 16 bytes per lane: the next
+// Record group g (256 bytes) of a slice holds 8 bytes per lane: the next
 // 16 / record-size records of the lane's state, padded with all-ones
 // records.  col[s] is the first group of slice s (col[n_slices] = total).
 // Records: 2 bytes = pos:14 | sign:1 | class:1, or 4 bytes = pos:22 |
@@ -123,7 +123,7 @@ struct ConnCache {
   CItem* items = nullptr;
   uint32_t* col = nullptr;       // [n_slices + 1]
   uint16_t* smap = nullptr;      // [n_slices * 32]
-  void* rec = nullptr;           // [n_groups * 512 bytes]
+  void* rec = nullptr;           // [n_groups * 256 bytes]
   double* c64 = nullptr;         // [n_cls] coefficient
   float* chi = nullptr;          // [n_cls] coefficient split in two floats
   float* clo = nullptr;
