@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kCT) hv_cached_kernel(const CArgs a, const Ham
   }
   using C = ChunkOf<T, VEC>;
   constexpr int kSPW = 32 / G;                   // states of a slice processed at once by a warp
-  constexpr int kU = VEC == 1 ? 8 : 2;           // record groups in flight per lane
+  constexpr int kU = VEC == 1 ? 8 : 4;           // record groups in flight per lane
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane % G, tg = lane / G;
   const bool lane_ok = tg < kSPW;                // G not dividing 32 leaves lanes idle
