@@ -145,14 +145,15 @@ __device__ __forceinline__ void state_sum(const unsigned char* rp, int ng, int n
 #pragma unroll
       for (int h = 0; h < RR::kPer; ++h) {
         if constexpr (sizeof(R) == 2) {
-          // branch-free: the sign flips the sign bit of x (exact), the class
-          // picks the sum; padding adds a zero (exact)
+          // branch-free: the sign flips the sign bit of x (exact); every hop
+          // goes into s0, class-1 hops also into s1 (class 0 = s0 - s1 at
+          // the end); padding adds a zero (exact)
           const bool c1 = (r[h] >> 15) & 1u;
           const uint32_t sg = (r[h] << 17) & 0x80000000u;
 #pragma unroll
           for (int u = 0; u < VEC; ++u) {
             const T v = flip_sign(xv[h][u], sg);
-            s0[u] += c1 ? T(0) : v;
+            s0[u] += v;
             s1[u] += c1 ? v : T(0);
           }
         } else {
@@ -180,7 +181,7 @@ __device__ __forceinline__ void state_sum(const unsigned char* rp, int ng, int n
     if (n_cls > 0) {
       const T ch = coef_hi<T>(c64, chi, 0), cl_ = coef_lo<T>(clo, 0);
 #pragma unroll
-      for (int u = 0; u < VEC; ++u) acc[u].fma(ch, cl_, s0[u]);
+      for (int u = 0; u < VEC; ++u) acc[u].fma(ch, cl_, s0[u] - s1[u]);
     }
     if (n_cls > 1) {
       const T ch = coef_hi<T>(c64, chi, 1), cl_ = coef_lo<T>(clo, 1);
