@@ -133,7 +133,10 @@ int mcd_build_basis(mcd_ctx* ctx, uint64_t seed, int64_t n_target, double beta,
 
 /* Install a basis given as host words (strictly ascending, all in the sector;
  * anything else is MCD_E_INVALID / MCD_E_SECTOR, nothing is sorted silently)
- * and build its device index. n >= 1. */
+ * and build its device index. n >= 1.  With a device the words are copied to
+ * it as they are and checked there (pinned host memory makes the copy a
+ * direct DMA); a host-only context checks and keeps them on the host.  The
+ * caller's array is not referenced after the call returns. */
 int mcd_set_basis(mcd_ctx* ctx, const uint64_t* host_words, int64_t n);
 /* Same as mcd_set_basis for words already in device memory (dev_words[n] on
  * the context's device).  Order and sector are checked on the device; the

@@ -229,6 +229,13 @@ class Context:
         return st, n.value
 
     def mcd_set_basis(self, words):
+        """Install a basis of host words: a numpy array / sequence, or a
+        contiguous 64-bit CPU torch tensor (pinned memory copies by DMA)."""
+        dev = getattr(words, "device", None)
+        if dev is not None and getattr(dev, "type", None) == "cpu" and hasattr(words, "data_ptr"):
+            if words.element_size() != 8 or not words.is_contiguous():
+                raise ValueError("basis tensor must be contiguous 64-bit words")
+            return self._check(self.L.mcd_set_basis(self.h, ctypes.cast(words.data_ptr(), c_u64p), words.numel()))
         w = np.ascontiguousarray(words, dtype=np.uint64)
         return self._check(self.L.mcd_set_basis(self.h, w.ctypes.data_as(c_u64p), len(w)))
 

@@ -447,6 +447,19 @@ int mcd_set_basis(mcd_ctx* c, const uint64_t* w, int64_t n) {
   if (!c->has_ham) return fail(c, MCD_E_STATE, "no Hamiltonian set");
   if (!w || n < 1) return fail(c, MCD_E_INVALID, "basis must hold at least one word");
   if (n > 0x7FFFFFFF) return fail(c, MCD_E_INVALID, "basis above 2^31 - 1 states");
+  if (has_device(c)) {
+    // straight to the device: the index build checks order and sector there
+    int st = need_device(c);
+    if (st != MCD_OK) return st;
+    c->basis.clear();
+    c->basis_on_host = false;
+    c->n_basis = 0;
+    c->gs_valid = false;
+    st = build_index(c, w, n, false);
+    if (st != MCD_OK) return st;
+    c->n_basis = n;
+    return MCD_OK;
+  }
   const int ns = c->n;
   const uint64_t half = ns == 32 ? 0xFFFFFFFFull : ((1ull << ns) - 1);
   for (int64_t k = 0; k < n; ++k) {
