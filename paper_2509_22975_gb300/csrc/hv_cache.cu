@@ -556,17 +556,21 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
         } else {
           span(it.lo, it.hi, 4, alo, ahi);            // basis index of each position
         }
-        const bool direct = rb > uint32_t(kSRecBytes) || xhi - xlo > int64_t(kSXBytes) || xhi > a.x_bytes;
+        // direct: the records do not fit (everything from global memory); x_out:
+        // only the x rows do not (they are gathered from global memory)
+        const bool direct = rb > uint32_t(kSRecBytes);
+        const bool x_out = xhi - xlo > int64_t(kSXBytes) || xhi > a.x_bytes;
         s_item[st] = it;
         s_sb[st] = sb;
-        s_direct[st] = direct ? 1 : 0;
+        s_direct[st] = direct ? 1 : (x_out ? 2 : 0);
         s_xoff[st] = int((int64_t(sb) * int64_t(sizeof(T)) - xlo) / int64_t(sizeof(T)));
         s_coff[st] = int((int64_t(it.slice0) * 4 - clo) / 4);
         s_aoff[st] = int((int64_t(it.lo) * (PASS_A ? 8 : 4) - alo) / (PASS_A ? 8 : 4));
         s_boff[st] = int((int64_t(it.lo) * int64_t(sizeof(T)) - blo) / int64_t(sizeof(T)));
         unsigned char* stage = s_dyn + st * kSStageBytes;
-        const uint32_t bytes =
-            direct ? 0u : rb + mb + uint32_t(chi - clo) + uint32_t(xhi - xlo) + uint32_t(ahi - alo) + uint32_t(bhi - blo);
+        const uint32_t bytes = direct ? 0u
+                                      : rb + mb + uint32_t(chi - clo) + (x_out ? 0u : uint32_t(xhi - xlo)) +
+                                            uint32_t(ahi - alo) + uint32_t(bhi - blo);
         if (bytes == 0u) {
           mbar_arrive(&s_full[st]);
         } else {
@@ -575,7 +579,7 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
           bulk_g2s(stage + kSOffMap, a.smap + int64_t(it.slice0) * 32, mb, &s_full[st]);
           bulk_g2s(stage + kSOffCol, reinterpret_cast<const unsigned char*>(a.col) + clo, uint32_t(chi - clo),
                    &s_full[st]);
-          if (xhi > xlo)
+          if (!x_out && xhi > xlo)
             bulk_g2s(stage + kSOffX, reinterpret_cast<const unsigned char*>(xg) + xlo, uint32_t(xhi - xlo),
                      &s_full[st]);
           const unsigned char* aux =
@@ -607,7 +611,15 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
                                      reinterpret_cast<const uint32_t*>(stage + kSOffAux) + s_aoff[st],
                                      reinterpret_cast<const T*>(stage + kSOffAux2) + s_boff[st], s_c64, s_chi,
                                      s_clo, s_dhi, s_dlo, s_d64, dh, dl);
-      } else {                   // too large for the stage: global memory
+      } else if (s_direct[st] == 2) {   // all but the x rows in the stage
+        const uint32_t* colp = reinterpret_cast<const uint32_t*>(stage + kSOffCol) + s_coff[st];
+        consume_item<T, PASS_A, DOT>(a, hp, it, s_sb[st], colp, stage,
+                                     reinterpret_cast<const uint16_t*>(stage + kSOffMap), xg + s_sb[st],
+                                     reinterpret_cast<const uint64_t*>(stage + kSOffAux) + s_aoff[st],
+                                     reinterpret_cast<const uint32_t*>(stage + kSOffAux) + s_aoff[st],
+                                     reinterpret_cast<const T*>(stage + kSOffAux2) + s_boff[st], s_c64, s_chi,
+                                     s_clo, s_dhi, s_dlo, s_d64, dh, dl);
+      } else {                   // records too large for the stage: global memory
         const uint32_t sb = s_sb[st];
         consume_item<T, PASS_A, DOT>(a, hp, it, sb, a.col + it.slice0, recg + int64_t(it.g0) * kGroup,
                                      a.smap + int64_t(it.slice0) * 32, xg + sb, a.words + it.lo, a.perm + it.lo,
