@@ -246,6 +246,24 @@ def impurity_batch(pkg, dev, n_inst=256, steps=400, tol=1e-6):
     return out
 
 
+def candidate_hops_per_state(words, lat_t, n_sites, sample=100_000, seed=0):
+    """Mean number of candidate hops per state (bonds, both spins, with exactly
+    one endpoint occupied: the enumeration before the lookup discards targets
+    outside the basis), on a random sample of the basis words."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    w = words[rng.choice(len(words), min(sample, len(words)), replace=False)].astype(np.uint64)
+    iu = np.argwhere(np.triu(lat_t, 1) != 0)
+    masks = np.array([(1 << int(i)) | (1 << int(j)) for i, j in iu], dtype=np.uint64)
+    half = np.uint64((1 << n_sites) - 1)
+    total = 0
+    for spin in (w >> np.uint64(n_sites), w & half):
+        for m in masks:
+            x = spin & m
+            total += int(np.count_nonzero((x != 0) & (x != m)))
+    return total / len(w), len(w)
+
+
 def cache_build_ms(pkg, ctx, n, dev):
     """Time of the first H~v of a basis (record build + one application)
     minus that of the next one (CUDA events, one column fp32)."""
@@ -446,6 +464,11 @@ def main():
                      "n_dn_blocks": info["n_dn_blocks"], "sampler_s": t_sample},
            "hv_cache": dict(cinfo, build_ms=build_ms),
            "E0_fp32": r32["E0"], "lanczos_iters_per_s_fp32": r32["iters"] / (ms * 1e-3)}
+    cand, cand_sample = candidate_hops_per_state(words, w.lat.t, w.n_sites)
+    out["candidate_hops"] = {"per_state": cand, "sample_states": cand_sample,
+                             "found_per_state": nnz / n,
+                             "per_s": world * cand * n * r32["iters"] / (ms * 1e-3),
+                             "note": "candidate hops (before the lookup) per second of the timed steps"}
 
     if args.hv_cols:
         # H~V with L columns (the band-Lanczos product), fp32, timed alone with
