@@ -652,19 +652,6 @@ __global__ void permute_kernel(const T* __restrict__ x, int ld, const uint32_t* 
 
 // ---- host ------------------------------------------------------------------------
 
-cudaError_t grow_bytes(void*& p, int64_t& cap, int64_t need, cudaStream_t s) {
-  if (p && cap >= need) return cudaSuccess;
-  if (p) cudaFreeAsync(p, s);
-  p = nullptr;
-  cap = 0;
-  cudaError_t e = cudaMallocAsync(&p, size_t(std::max<int64_t>(need, 16)), s);
-  if (e != cudaSuccess) {
-    p = nullptr;
-    return e;
-  }
-  cap = need;
-  return cudaSuccess;
-}
 template <typename P>
 cudaError_t grow(P*& p, int64_t& cap, int64_t need, size_t elem, cudaStream_t s) {
   void* q = p;
@@ -983,7 +970,7 @@ void cache_invalidate(Layout& L) {
 void free_cache(Layout& L) {
   ConnCache& cc = L.cc;
   auto f = [](void* p) { if (p) cudaFree(p); };
-  f(cc.items); f(cc.col); f(cc.smap); f(cc.rec); f(cc.c64); f(cc.xb); f(cc.yb);
+  f(cc.items); f(cc.col); f(cc.smap); f(cc.rec); f(cc.c64); f(cc.xb); f(cc.yb); f(cc.xbm);
   cc = ConnCache();
 }
 

@@ -52,6 +52,7 @@ struct CArgs {
   const void* x;
   void* y;
   const void* xb;                // pass B of the streaming kernel: x in layout order
+  int x_layout;                  // many-column kernel: rows of x are in this layout's order
   void* yb;                      // streaming kernels: pass B's part of y (basis order), read by pass A
   int ncols, ld;
   int ncp;                       // staged row stride (elements)
@@ -206,6 +207,21 @@ __device__ __forceinline__ Coef<T> diag_of(const HamParams& hp, const float* dhi
 }
 
 // ---- host ------------------------------------------------------------------------
+
+// (re)allocates p to at least need bytes, stream-ordered
+inline cudaError_t grow_bytes(void*& p, int64_t& cap, int64_t need, cudaStream_t s) {
+  if (p && cap >= need) return cudaSuccess;
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMallocAsync(&p, size_t(std::max<int64_t>(need, 16)), s);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    return e;
+  }
+  cap = need;
+  return cudaSuccess;
+}
 
 inline void fill_args(mcd_ctx* c, const Layout& L, CArgs& a) {
   const ConnCache& cc = L.cc;

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(kCT) hv_cached_kernel(const CArgs a, const Ham
   const unsigned char* recg = static_cast<const unsigned char*>(a.rec);
   const uint32_t half = a.n_sites >= 32 ? 0xFFFFFFFFu : ((1u << a.n_sites) - 1u);
   const int ld = a.ld, ncp = a.ncp;
+  const int ldx = a.x_layout ? ncp : ld;   // row stride of x (pass B may read the dn-major copy)
 
   for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
     const CItem it = a.items[item];
@@ -53,9 +54,9 @@ __global__ void __launch_bounds__(kCT) hv_cached_kernel(const CArgs a, const Ham
     __syncthreads();   // the previous item's rows are no longer read
     if (staged && lane_ok && cvalid > 0) {
       for (int q = warp * kSPW + tg; q < nst; q += kCWarps * kSPW) {
-        const int64_t row = PASS_A ? int64_t(sb) + q : int64_t(__ldg(a.perm + sb + q));
+        const int64_t row = (PASS_A || a.x_layout) ? int64_t(sb) + q : int64_t(__ldg(a.perm + sb + q));
         T v[VEC];
-        C::load(x + row * ld + col0, cvalid, v);
+        C::load(x + row * ldx + col0, cvalid, v);
 #pragma unroll
         for (int u = 0; u < VEC; ++u) xs[q * ncp + col0 + u] = v[u];
       }
@@ -67,8 +68,8 @@ __global__ void __launch_bounds__(kCT) hv_cached_kernel(const CArgs a, const Ham
 #pragma unroll
         for (int u = 0; u < VEC; ++u) v[u] = xs[q * ncp + col0 + u];
       } else {
-        const int64_t row = PASS_A ? int64_t(sb) + q : int64_t(__ldg(a.perm + sb + q));
-        C::load(x + row * ld + col0, cvalid, v);
+        const int64_t row = (PASS_A || a.x_layout) ? int64_t(sb) + q : int64_t(__ldg(a.perm + sb + q));
+        C::load(x + row * ldx + col0, cvalid, v);
       }
     };
     const int nsl = int((it.hi - it.lo + 31) / 32);
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kCT) hv_cached_kernel(const CArgs a, const Ham
 #pragma unroll
             for (int u = 0; u < VEC; ++u) xk[u] = xs[int(k - sb) * ncp + col0 + u];
           } else {
-            C::load(x + int64_t(k) * ld + col0, cvalid, xk);
+            C::load(x + int64_t(k) * ldx + col0, cvalid, xk);
           }
           C::load(y + int64_t(k) * ld + col0, cvalid, yk);
           const Coef<T> dc = diag_of<T>(hp, s_dhi, s_dlo, s_d64, up, dn);
@@ -119,6 +120,22 @@ __global__ void __launch_bounds__(kCT) hv_cached_kernel(const CArgs a, const Ham
   }
 }
 
+// X in the dn-major order: xb[k][:] = x[perm[k]][:] (ncp columns per row of xb,
+// VEC-column chunks; the padding columns of xb are zero)
+template <typename T, int VEC>
+__global__ void permute_rows_kernel(const T* __restrict__ x, int ld, int ncols, int ncp,
+                                    const uint32_t* __restrict__ perm, int64_t n, T* __restrict__ xb) {
+  using C = ChunkOf<T, VEC>;
+  const int chunks = ncp / VEC;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n * chunks) return;
+  const int64_t k = i / chunks;
+  const int col0 = int(i % chunks) * VEC;
+  T v[VEC];
+  C::load(x + int64_t(__ldg(perm + k)) * ld + col0, ncols - col0, v);
+  C::store(xb + k * ncp + col0, ncp - col0, v);
+}
+
 template <typename T, int VEC, int G>
 cudaError_t launch_cached(mcd_ctx* c, const void* x, void* y, int ncols, int ld) {
   const int chunks = (ncols + VEC - 1) / VEC;
@@ -131,6 +148,14 @@ cudaError_t launch_cached(mcd_ctx* c, const void* x, void* y, int ncols, int ld)
     cudaFuncSetAttribute(hv_cached_kernel<T, VEC, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     configured = smem;
   }
+  // pass B reads X in the dn-major order, copied once (rows contiguous like pass A's)
+  ConnCache& cb = c->idx.B.cc;
+  const int64_t n = c->idx.n;
+  const bool permuted = G > 1 && n > 0;
+  if (permuted) {
+    cudaError_t e = grow_bytes(cb.xbm, cb.xbm_cap, n * ncp * int64_t(sizeof(T)), c->stream);
+    if (e != cudaSuccess) return e;
+  }
   for (int pass = 0; pass < 2; ++pass) {
     const Layout& L = pass == 0 ? c->idx.B : c->idx.A;
     CArgs a;
@@ -140,6 +165,15 @@ cudaError_t launch_cached(mcd_ctx* c, const void* x, void* y, int ncols, int ld)
     a.ncols = ncols;
     a.ld = ld;
     a.ncp = ncp;
+    if (pass == 0 && permuted) {
+      const int64_t work = n * (ncp / VEC);
+      permute_rows_kernel<T, VEC><<<int((work + 255) / 256), 256, 0, c->stream>>>(
+          static_cast<const T*>(x), ld, ncols, ncp, L.perm, n, static_cast<T*>(cb.xbm));
+      MCD_LAUNCHED(c);
+      a.x = cb.xbm;
+      // rows of the copy are ncp elements apart (the kernel's ldx); y keeps ld
+      a.x_layout = 1;
+    }
     a.off_xs = off_xs;
     a.xs_cap = int(kMStageBytes / sizeof(T));
     if (a.n_items <= 0) continue;

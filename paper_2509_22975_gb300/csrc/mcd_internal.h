@@ -128,9 +128,10 @@ struct ConnCache {
   float* chi = nullptr;          // [n_cls] coefficient split in two floats
   float* clo = nullptr;
   void* xb = nullptr;            // x in this layout's order (streaming kernel of pass B)
+  void* xbm = nullptr;           // X (many columns) in this layout's order (pass B)
   void* yb = nullptr;            // pass B's part of y (streaming kernels), read by pass A
   unsigned int* err = nullptr;   // set by a kernel whose bounded wait ran out
-  int64_t items_cap = 0, col_cap = 0, smap_cap = 0, rec_cap = 0, cls_cap = 0, xb_cap = 0, yb_cap = 0;
+  int64_t items_cap = 0, col_cap = 0, smap_cap = 0, rec_cap = 0, cls_cap = 0, xb_cap = 0, yb_cap = 0, xbm_cap = 0;
 };
 
 struct Layout {
