@@ -208,3 +208,30 @@ def test_band_green_with_and_without_cache():
         out.append((G, dp, dm))
     assert out[0][1:] == out[1][1:]
     assert np.max(np.abs(out[0][0] - out[1][0])) < 1e-9 * max(1.0, np.max(np.abs(out[0][0])))
+
+
+def test_set_basis_from_pinned_tensor_and_device_checks():
+    # host words go straight to the device and are checked there: a pinned
+    # torch tensor gives the same basis and products as a numpy array;
+    # unsorted words and words outside the sector are refused with the same
+    # codes as on a host-only context, and the context stays usable
+    w = C.tilted12_u8()
+    ctx = device_ctx(w, nf=5000)
+    B = ctx.mcd_get_basis()
+    P = H.build(model(w), B)
+    t = torch.from_numpy(B.view(np.int64)).pin_memory()
+    ctx.mcd_set_basis(t)
+    assert np.array_equal(ctx.mcd_get_basis(), B)
+    check(ctx, P, w.lat.t, 1, np.float64)
+    bad = B.copy()
+    bad[[10, 11]] = bad[[11, 10]]
+    with pytest.raises(pkg.MCDError) as e:
+        ctx.mcd_set_basis(bad)
+    assert e.value.status == -1
+    up = (1 << 12) - 1                       # 12 up electrons: outside the 6 + 6 sector
+    outside = np.sort(np.concatenate([B[:100], np.array([(up << 12) | 0b111111], dtype=np.uint64)]))
+    with pytest.raises(pkg.MCDError) as e:
+        ctx.mcd_set_basis(np.unique(outside))
+    assert e.value.status == -2
+    ctx.mcd_set_basis(B)
+    check(ctx, P, w.lat.t, 3, np.float32)
