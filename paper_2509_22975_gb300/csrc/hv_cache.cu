@@ -642,12 +642,27 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
   if constexpr (DOT) dot_reduce<SCfg<T>::kCons + 1>(a, double(dh) + double(dl), s_red);
 }
 
-// x in the layout's order: xb[k] = x[perm[k]] (one column, stride ld)
+// x in the layout's order: xb[k] = x[perm[k]] (one column), four positions per
+// thread: one 16-byte load of perm, four gathers, 16-byte stores (perm and xb
+// start on 16-byte boundaries; the last n % 4 positions one by one)
 template <typename T>
-__global__ void permute_kernel(const T* __restrict__ x, int ld, const uint32_t* __restrict__ perm, int64_t n,
+__global__ void permute_kernel(const T* __restrict__ x, const uint32_t* __restrict__ perm, int64_t n,
                                T* __restrict__ xb) {
-  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k < n) xb[k] = x[int64_t(perm[k]) * ld];
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nq = n / 4;
+  if (q < nq) {
+    const uint4 p = __ldg(reinterpret_cast<const uint4*>(perm) + q);
+    const T v0 = __ldg(x + p.x), v1 = __ldg(x + p.y), v2 = __ldg(x + p.z), v3 = __ldg(x + p.w);
+    if constexpr (sizeof(T) == 4) {
+      reinterpret_cast<float4*>(xb)[q] = make_float4(v0, v1, v2, v3);
+    } else {
+      reinterpret_cast<double2*>(xb)[2 * q] = make_double2(v0, v1);
+      reinterpret_cast<double2*>(xb)[2 * q + 1] = make_double2(v2, v3);
+    }
+  } else if (q < nq + (n - 4 * nq)) {
+    const int64_t k = 4 * nq + (q - nq);
+    xb[k] = x[perm[k]];
+  }
 }
 
 // ---- host ------------------------------------------------------------------------
@@ -928,8 +943,9 @@ cudaError_t launch_stream(mcd_ctx* c, const void* x, void* y, double* partials, 
     }
     timing_begin(c, pass == 0 ? 0 : 1);
     if (pass == 0) {
-      permute_kernel<T><<<int((n + 255) / 256), 256, 0, c->stream>>>(static_cast<const T*>(x), 1, L.perm, n,
-                                                                     static_cast<T*>(cb.xb));
+      const int64_t threads = n / 4 + n % 4;
+      permute_kernel<T><<<int((threads + 255) / 256), 256, 0, c->stream>>>(static_cast<const T*>(x), L.perm, n,
+                                                                           static_cast<T*>(cb.xb));
       MCD_LAUNCHED(c);
       hv_stream_kernel<T, false, false><<<int(grid), SCfg<T>::kThreads, smem, c->stream>>>(a, *c->hp);
     } else if (dot) {
