@@ -235,3 +235,18 @@ def test_set_basis_from_pinned_tensor_and_device_checks():
     assert e.value.status == -2
     ctx.mcd_set_basis(B)
     check(ctx, P, w.lat.t, 3, np.float32)
+
+
+@pytest.mark.parametrize("cut", [1, 2, 3, 5])
+def test_single_column_basis_size_not_a_multiple_of_four(cut):
+    # the dn-major copy of x before pass B moves four positions per thread;
+    # the last n mod 4 positions take the scalar tail
+    w = C.square16_u8()
+    ctx = device_ctx(w, nf=40000)
+    B = ctx.mcd_get_basis()[:-cut]
+    P = H.build(model(w), B)
+    ctx = cached_ctx(w, B)
+    for dtype in (np.float32, np.float64):
+        check(ctx, P, w.lat.t, 1, dtype, seed=cut)
+    info = ctx.mcd_hv_cache_info()
+    assert info["n_conn"] == P.nnz_offdiag() and info["wait_errors"] == 0
