@@ -59,7 +59,7 @@ def test_autograd_hv():
 
 
 def test_ground_energy_gradient_vs_finite_differences():
-    # spec bar: adjoint gradients within 1e-6 of finite differences
+    # adjoint gradients agree with central finite differences to 1e-6
     w = C.ring8_u4()
     ctx = device_ctx(w)
     t = torch.tensor(w.lat.t, dtype=torch.float64, requires_grad=True)
