@@ -334,7 +334,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--hv-cols", type=int, nargs="*", default=[1, 24])
+    ap.add_argument("--hv-cols", type=int, nargs="*", default=[1, 8, 24])
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-impurity batch measurement")
     ap.add_argument("--no-hv-cache", action="store_true",
                     help="matrix-free H*v kernels (no connection records) on the 4x4 workload")
