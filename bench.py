@@ -449,7 +449,8 @@ def main():
     h2d = n * 8
     e2e = {"value": world * conns_per_step / e2e_s / 1e9 if args.e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
-           "path": "mcd_set_basis(pinned host words) + mcd_lanczos_ground + E0 to host"}
+           "path": "mcd_set_basis(pinned host words) + mcd_lanczos_ground + E0 to host",
+           "note": "runs without the per-kernel CUDA events that the device-timed steps record for the roofline"}
 
     # the record build alone: a fresh basis, first H~v minus the next one
     ctx.mcd_set_basis_device(words_dev)
