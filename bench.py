@@ -49,6 +49,23 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def slowest_rank_ms(ms: float, dist, dev) -> float:
+    """Step time of the slowest rank, received by every rank (one rank: ms).
+    Each rank runs its own replica of the step, so the job ends with it."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_step: float, ms: float) -> float:
+    """Units of all ranks per second, in 1e9 (every rank processes
+    units_per_step per step; ms = the slowest rank's step time)."""
+    return world * units_per_step / (ms * 1e-3) / 1e9
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -404,12 +421,9 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     kms, kcnt = ctx.mcd_kernel_times(reset=True)
     ctx.mcd_set_option(pkg.MCD_OPT_KERNEL_TIMING, 0)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank_ms(ms, dist, dev)
     conns_per_step = nnz * r32["iters"]
-    value = world * conns_per_step / (ms * 1e-3) / 1e9
+    value = whole_job_rate(world, conns_per_step, ms)
 
     # roofline of the H~v pair (pass B: dn-major up-hop kernel, pass A: up-major dn-hop + diagonal)
     tB = kms[0] / max(kcnt[0], 1)
