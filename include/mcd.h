@@ -144,6 +144,21 @@ int mcd_set_basis(mcd_ctx* ctx, const uint64_t* host_words, int64_t n);
 int mcd_set_basis_device(mcd_ctx* ctx, const uint64_t* dev_words, int64_t n);
 /* Copy the basis to host_out[cap]; *n = basis size (also when cap is short). */
 int mcd_get_basis(const mcd_ctx* ctx, uint64_t* host_out, int64_t cap, int64_t* n);
+/* Basis file (checkpoint of a sampled truncated basis F~, Sec. "Subspace of
+ * the ground state"): mcd_save_basis writes the installed basis to path as a
+ * 40-byte little-endian header (magic "MCDBASIS", version 1, n_sites, N_up,
+ * N_dn as uint32, N_f as int64, FNV-1a 64-bit hash of the words' bytes)
+ * followed by the N_f uint64 words; MCD_E_STATE without a Hamiltonian or a
+ * basis, MCD_E_INVALID if the file cannot be written.  mcd_load_basis reads
+ * such a file and installs it as mcd_set_basis would: MCD_E_STATE without a
+ * Hamiltonian, MCD_E_SECTOR if the file's sector differs from the
+ * Hamiltonian's, MCD_E_INVALID for a missing, short, foreign or corrupted file
+ * (magic, version, size or hash) and for words out of order.  A file
+ * rejected before its words are checked (magic, version, sector, size, hash)
+ * leaves the current basis in place.  path is a NUL-terminated file name, not
+ * referenced after the call. */
+int mcd_save_basis(const mcd_ctx* ctx, const char* path);
+int mcd_load_basis(mcd_ctx* ctx, const char* path);
 /* Sizes of the installed basis and its index; nnz_offdiag = number of nonzero
  * off-diagonal entries of H~ (counted on the device; pass NULL to skip). */
 int mcd_basis_info(mcd_ctx* ctx, int64_t* n_states, int64_t* n_up_blocks,

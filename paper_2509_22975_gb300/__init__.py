@@ -47,6 +47,8 @@ _SIGS = {
     "mcd_set_basis": (ctypes.c_int, [c_vp, c_u64p, ctypes.c_int64]),
     "mcd_set_basis_device": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64]),
     "mcd_get_basis": (ctypes.c_int, [c_vp, c_u64p, ctypes.c_int64, c_i64p]),
+    "mcd_save_basis": (ctypes.c_int, [c_vp, ctypes.c_char_p]),
+    "mcd_load_basis": (ctypes.c_int, [c_vp, ctypes.c_char_p]),
     "mcd_launch_count": (ctypes.c_int, [c_vp, c_i64p]),
     "mcd_hv_cache_info": (ctypes.c_int, [c_vp, c_i64p, c_i64p, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
@@ -243,6 +245,13 @@ class Context:
         """Install a basis held in a device uint64/int64 torch tensor."""
         self._sync_stream()
         return self._check(self.L.mcd_set_basis_device(self.h, _ptr(words), words.numel()))
+
+    def mcd_save_basis(self, path):
+        self._check(self.L.mcd_save_basis(self.h, os.fsencode(path)))
+
+    def mcd_load_basis(self, path):
+        self._sync_stream()
+        self._check(self.L.mcd_load_basis(self.h, os.fsencode(path)))
 
     def mcd_launch_count(self) -> int:
         n = ctypes.c_int64(0)
