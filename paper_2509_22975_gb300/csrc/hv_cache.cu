@@ -5,9 +5,10 @@
 // the basis and the Hamiltonian, so Lanczos (hundreds of H~x with the same
 // H~) and band Lanczos (hundreds of H~V) would otherwise enumerate and look
 // up the same hops every step.  The first H~x of a basis runs the
-// enumeration and the in-block lookup of both passes once (the bond loop,
-// masked-popcount sign and in-block binary search of the matrix-free block
-// kernels) and writes what it finds as records:
+// enumeration and the in-block lookup of both passes once (the bond loop and
+// masked-popcount sign of the matrix-free kernels; a shared bitmap of the
+// block for n <= 16 sites, binary search otherwise) and writes what it finds
+// as records:
 //   2 bytes  position:14 | sign:1 | amplitude class:1   (<= 2 amplitudes)
 //   4 bytes  position:22 | sign:1 | class:9             (otherwise, or an
 //            item whose blocks hold more than 16383 states)
@@ -23,20 +24,23 @@
 // (sliced ELL with sorting inside the item), so one warp reads one slice
 // with every load aligned, little padding and no per-state offsets.
 //
-// Sums keep the arithmetic of the matrix-free kernels: per state, hops of
-// one amplitude class are summed first, then multiplied by the class's fp64
-// amplitude (split into two floats for fp32 vectors).
+// Per state, the hops are summed per amplitude class and each sum is then
+// multiplied by the class's fp64 amplitude (split into two floats for fp32
+// vectors); with 2-byte records the class-0 sum is the sum of all hops minus
+// the class-1 sum.  The order of every sum is fixed, so results repeat bit
+// for bit.
 //
 // One column (Lanczos): a persistent warp-specialised kernel.  One producer
 // thread moves each item's records, lane map, slice offsets, staged x rows
 // and per-state words into shared memory with bulk asynchronous copies
 // (cp.async.bulk, completion counted on an mbarrier), two stages deep,
-// while eight consumer warps work on the previous item from shared memory
-// and only store to global memory.  Pass B reads x in its own (dn-major)
+// while 12 (fp32 vectors) or 8 (fp64) consumer warps work on the previous
+// item from shared memory and only store to global memory.  Pass B reads x in its own (dn-major)
 // order from a permuted copy, so that its rows are contiguous, and writes
 // its part of y to a scratch vector that pass A streams in.
 // Many columns (band Lanczos): CTAs stage x rows of an item with ordinary
-// loads and groups of G lanes share a state.
+// loads and groups of G lanes share a state; pass B reads a dn-major copy of
+// X.
 #include <algorithm>
 #include <vector>
 
