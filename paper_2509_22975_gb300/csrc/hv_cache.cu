@@ -39,8 +39,8 @@
 // order from a permuted copy, so that its rows are contiguous, and writes
 // its part of y to a scratch vector that pass A streams in.
 // Many columns (band Lanczos): CTAs stage x rows of an item with ordinary
-// loads and groups of G lanes share a state; pass B reads a dn-major copy of
-// X.
+// loads and groups of G lanes share a state; with G > 1, pass B reads a
+// dn-major copy of X.
 #include <algorithm>
 #include <vector>
 

@@ -2,8 +2,9 @@
 // with a row stride: a CTA per work item stages the x rows of the item's
 // stage range in shared memory when they fit (else gathers from global
 // memory) and groups of G lanes share a state, lane g owning VEC columns.
-// Pass B (up-spin hops, dn-major blocks) reads a dn-major copy of X made by
-// permute_rows_kernel, so that the rows of its blocks are contiguous.
+// With several lanes per state (G > 1), pass B (up-spin hops, dn-major
+// blocks) reads a dn-major copy of X made by permute_rows_kernel, so that the
+// rows of its blocks are contiguous; with G = 1 it gathers through perm.
 // The records and their layout are those of hv_cache.cu.
 #include <algorithm>
 
