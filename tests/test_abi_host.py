@@ -171,3 +171,33 @@ def test_sampler_placement_option_on_host_context():
     for bad in (-1, 3):
         with pytest.raises(pkg.MCDError):
             ctx.mcd_set_option(pkg.MCD_OPT_SAMPLER_DEVICE, bad)
+
+
+def test_option_ranges():
+    # every documented value is taken; values outside the documented range and
+    # unknown options are MCD_E_INVALID
+    ctx = pkg.Context(-1)
+    ok = {pkg.MCD_OPT_HV_ALGO: [0, 1, 2, 3], pkg.MCD_OPT_KERNEL_TIMING: [0, 1],
+          pkg.MCD_OPT_SAMPLER_THREADS: [0, 1, 16], pkg.MCD_OPT_SAMPLER_DEVICE: [0, 1, 2],
+          pkg.MCD_OPT_HV_CACHE: [0, 1, 2], pkg.MCD_OPT_HASH_ITEM: [64, 128, 1024, 4096]}
+    bad = {pkg.MCD_OPT_HV_ALGO: [-1, 4], pkg.MCD_OPT_SAMPLER_THREADS: [-1],
+           pkg.MCD_OPT_SAMPLER_DEVICE: [-1, 3], pkg.MCD_OPT_HV_CACHE: [-1, 3],
+           pkg.MCD_OPT_HASH_ITEM: [0, 32, 63, 100, 8192], 999: [0]}
+    for opt, vals in ok.items():
+        for v in vals:
+            ctx.mcd_set_option(opt, v)
+    for opt, vals in bad.items():
+        for v in vals:
+            with pytest.raises(pkg.MCDError) as e:
+                ctx.mcd_set_option(opt, v)
+            assert e.value.status == -1, (opt, v)
+
+
+def test_device_work_on_a_host_context():
+    w = C.ring8_u4()
+    ctx = host_ctx(w)
+    ctx.mcd_set_basis(np.array([w.seed_word()], dtype=np.uint64))
+    with pytest.raises(pkg.MCDError) as e:
+        ctx.mcd_lanczos_ground(10, 1e-6, 0, pkg.MCD_F64)
+    assert e.value.status == -9
+    assert ctx.mcd_hv_cache_info() == {"bytes": 0, "n_conn": 0, "rec_bytes": 0, "wait_errors": 0}
