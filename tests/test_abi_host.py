@@ -201,3 +201,17 @@ def test_device_work_on_a_host_context():
         ctx.mcd_lanczos_ground(10, 1e-6, 0, pkg.MCD_F64)
     assert e.value.status == -9
     assert ctx.mcd_hv_cache_info() == {"bytes": 0, "n_conn": 0, "rec_bytes": 0, "wait_errors": 0}
+
+
+def test_every_status_code_has_its_own_string():
+    import re
+    text = open(pkg.HEADER).read()
+    enum = text[text.index("typedef enum {"):text.index("} mcd_status;")]
+    codes = {name: int(v) for name, v in re.findall(r"(MCD_[A-Z_]+)\s*=\s*(-?\d+)", enum)}
+    assert codes["MCD_OK"] == 0 and len(codes) == 11
+    L_ = pkg.lib()
+    strings = {c: L_.mcd_status_string(c) for c in codes.values()}
+    assert b"unknown status" not in strings.values()
+    assert len(set(strings.values())) == len(codes)
+    assert L_.mcd_status_string(min(codes.values()) - 1) == b"unknown status"
+    assert L_.mcd_status_string(max(codes.values()) + 1) == b"unknown status"
