@@ -1,0 +1,46 @@
+"""The benchmark's candidate-hop count (bonds with exactly one endpoint
+occupied, both spins) against the oracle's hop enumeration state by state, and
+its full-sector mean against the closed form bonds * 2 k (n - k) / (n (n - 1))
+per spin (k electrons of that spin on n sites)."""
+import os
+import sys
+
+import numpy as np
+
+from oracle import fock
+from workloads import configs as C
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def closed_form(bonds, n, ks):
+    return sum(bonds * 2 * k * (n - k) / (n * (n - 1)) for k in ks)
+
+
+def test_full_sector_mean_is_the_closed_form():
+    for w in (C.ring8_u4(), C.tilted12_u8()):
+        n = w.n_sites
+        B = fock.sector(n, w.n_up, w.n_dn)
+        if len(B) > 20000:
+            B = B[np.random.default_rng(0).choice(len(B), 20000, replace=False)]
+            tol = 0.05 * closed_form(np.count_nonzero(np.triu(w.lat.t, 1)), n, (w.n_up, w.n_dn))
+        else:
+            tol = 1e-12
+        mean, used = bench.candidate_hops_per_state(B, w.lat.t, n, sample=len(B))
+        assert used == len(B)
+        ref = closed_form(np.count_nonzero(np.triu(w.lat.t, 1)), n, (w.n_up, w.n_dn))
+        assert abs(mean - ref) <= tol, (w.name, mean, ref)
+    # the figures quoted for the ring and the 4x4: 9.14 and 67.2 per state
+    assert abs(closed_form(8, 8, (4, 4)) - 64 / 7) < 1e-12
+    assert abs(closed_form(64, 16, (7, 7)) - 67.2) < 1e-12
+
+
+def test_counts_equal_allowed_directed_hops():
+    w = C.ring8_u4()
+    n = w.n_sites
+    B = fock.sector(n, w.n_up, w.n_dn)[::37]
+    hops = fock.directed_hops(w.lat.t)
+    allowed = sum(1 for x in B for spin in (0, 1) for i, j, _ in hops if fock.hop_word(int(x), n, spin, i, j))
+    mean, used = bench.candidate_hops_per_state(B, w.lat.t, n, sample=len(B))
+    assert used == len(B) and abs(mean * len(B) - allowed) < 1e-9
