@@ -44,3 +44,23 @@ def test_counts_equal_allowed_directed_hops():
     allowed = sum(1 for x in B for spin in (0, 1) for i, j, _ in hops if fock.hop_word(int(x), n, spin, i, j))
     mean, used = bench.candidate_hops_per_state(B, w.lat.t, n, sample=len(B))
     assert used == len(B) and abs(mean * len(B) - allowed) < 1e-9
+
+
+def test_traffic_is_reported_only_for_the_captured_sources(tmp_path, monkeypatch):
+    import json
+    import shutil
+    src = os.path.join(bench.ROOT, "paper_2509_22975_gb300", "csrc")
+    dst = tmp_path / "paper_2509_22975_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in ("hv_cache.cu", "hv_cache.cuh", "hv_common.cuh"):
+        shutil.copy(os.path.join(src, f), dst / f)
+    (tmp_path / "profiles").mkdir()
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), tmp_path / "profiles" / "traffic.json")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    key = "hv_cached_pass_B_square16_fp32_L1"
+    rec = json.load(open(tmp_path / "profiles" / "traffic.json"))[key]
+    assert bench.traffic_for(key) == rec["bytes_per_launch"] == rec["read"] + rec["write"]
+    assert bench.traffic_for("no_such_kernel") is None
+    with open(dst / "hv_cache.cuh", "a") as f:       # any change to the kernel sources
+        f.write("\n")
+    assert bench.traffic_for(key) is None
