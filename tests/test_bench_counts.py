@@ -47,19 +47,22 @@ def test_counts_equal_allowed_directed_hops():
 
 
 def test_traffic_is_reported_only_for_the_captured_sources(tmp_path, monkeypatch):
+    import hashlib
     import json
     import shutil
     src = os.path.join(bench.ROOT, "paper_2509_22975_gb300", "csrc")
     dst = tmp_path / "paper_2509_22975_gb300" / "csrc"
     dst.mkdir(parents=True)
+    h = hashlib.sha256()
     for f in ("hv_cache.cu", "hv_cache.cuh", "hv_common.cuh"):
         shutil.copy(os.path.join(src, f), dst / f)
+        h.update((dst / f).read_bytes())
     (tmp_path / "profiles").mkdir()
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), tmp_path / "profiles" / "traffic.json")
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     key = "hv_cached_pass_B_square16_fp32_L1"
-    rec = json.load(open(tmp_path / "profiles" / "traffic.json"))[key]
-    assert bench.traffic_for(key) == rec["bytes_per_launch"] == rec["read"] + rec["write"]
+    rec = {"read": 400, "write": 72, "bytes_per_launch": 472, "kernel_src_sha": h.hexdigest()[:16]}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({key: rec}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_for(key) == 472
     assert bench.traffic_for("no_such_kernel") is None
     with open(dst / "hv_cache.cuh", "a") as f:       # any change to the kernel sources
         f.write("\n")
