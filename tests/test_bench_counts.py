@@ -1,7 +1,9 @@
 """The benchmark's candidate-hop count (bonds with exactly one endpoint
 occupied, both spins) against the oracle's hop enumeration state by state, and
 its full-sector mean against the closed form bonds * 2 k (n - k) / (n (n - 1))
-per spin (k electrons of that spin on n sites)."""
+per spin (k electrons of that spin on n sites); and the DRAM-traffic lookup,
+which reports a captured figure only while the kernel sources hash to the
+value recorded with it."""
 import os
 import sys
 
