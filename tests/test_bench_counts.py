@@ -69,3 +69,13 @@ def test_traffic_is_reported_only_for_the_captured_sources(tmp_path, monkeypatch
     with open(dst / "hv_cache.cuh", "a") as f:       # any change to the kernel sources
         f.write("\n")
     assert bench.traffic_for(key) is None
+
+
+def test_peak_from_the_measured_file_else_the_fallback(tmp_path, monkeypatch):
+    import json
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peak, src = bench.measured_peak()
+    assert peak == bench.FALLBACK_HBM and src.startswith("fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6789.3, "bf16_tflops": 1941.7}))
+    peak, src = bench.measured_peak()
+    assert peak == 6789.3 and src.startswith("measured")
