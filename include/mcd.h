@@ -118,8 +118,9 @@ int mcd_set_hamiltonian(mcd_ctx* ctx, int n_sites, const double* t, const double
 /* Sec. "Subspace of the ground state": grow F~ from the seed words by steps,
  * proposing every hopping term of every starting state and accepting a
  * proposed state b with probability min(exp(-beta sum_i U_i n_i,up n_i,dn(b)), 1).
- * Random draws: SplitMix64, keyed by (seed, step, parent word, hop id);
- * the full rule is in the design notes and is shared with the oracle.
+ * Random draws: one uniform number per proposal from SplitMix64 (its
+ * published output function), keyed by (seed, step, parent word, hop id), so
+ * the draws do not depend on where or in which order proposals are made.
  * seed_states: host [n_seed] >= 1 words of the sector.  Stops at exactly
  * n_target states (a final overshooting step keeps the new states of smallest
  * SplitMix64 priority), or earlier if no new state appears for 64 steps
