@@ -48,7 +48,7 @@ typedef enum {
   MCD_E_CUDA = -4,            /* a CUDA call failed (message in last_error) */
   MCD_E_NOT_CONVERGED = -5,   /* Lanczos hit max_iter above tolerance */
   MCD_E_BREAKDOWN = -6,       /* non-finite Lanczos coefficient */
-  MCD_E_TIMEOUT = -7,         /* reserved: bounded device wait expired */
+  MCD_E_TIMEOUT = -7,         /* a bounded device wait gave up: the product is incomplete */
   MCD_E_STATE = -8,           /* call out of order (no Hamiltonian / basis) */
   MCD_E_NODEVICE = -9         /* device work asked of a host-only context */
 } mcd_status;
@@ -86,6 +86,22 @@ typedef enum { MCD_F64 = 0, MCD_F32 = 1 } mcd_dtype;
                                    built).  Only with MCD_OPT_HV_ALGO = 0.
                                    The result is the same matrix, summed in
                                    another order (within rounding). */
+#define MCD_OPT_APPLY_SYNC 7     /* 1 = mcd_apply waits for its product and
+                                   returns MCD_E_TIMEOUT when a bounded wait
+                                   of the streaming kernel gave up (default);
+                                   0 = mcd_apply returns after the launch and
+                                   such a failure is reported by the next call
+                                   that reads it (mcd_apply with 1,
+                                   mcd_lanczos_ground, mcd_band_lanczos_green,
+                                   mcd_hv_cache_info).  A reported failure is
+                                   cleared, so later calls can succeed. */
+#define MCD_OPT_WAIT_TEST 8      /* test of the time-out path: value k >= 0
+                                   makes the next one-column cached product
+                                   withhold the shared-memory copies of work
+                                   item k of its second pass and poll each
+                                   wait only 4096 times, so that the waits on
+                                   that item give up; -1 = off (default).
+                                   Applies to one product, then resets. */
 #define MCD_OPT_HASH_ITEM 4     /* states per work item of the hash-lookup
                                    kernels: a power of two in [64, 4096]
                                    (default 1024).  Blocks of more states are
@@ -195,15 +211,17 @@ int mcd_connections(mcd_ctx* ctx, int64_t* rows_dev, int64_t* cols_dev, double* 
 
 /* No counterpart in the paper: the same output as mcd_connections, for
  * callers that must not allocate device memory (a caller whose memory is all
- * owned by its own pool, one under a fixed memory budget, one recording into
- * a CUDA graph).  The per-row counts and offsets live in one fixed 2 MiB
- * array of device global memory that the library defines, so this call
+ * owned by its own pool, or one under a fixed memory budget where a late
+ * allocation can fail).  The per-row counts and offsets live in one fixed
+ * 2 MiB array of device global memory that the library defines, so this call
  * allocates nothing; every GPU that loads the library keeps that array until
  * the process exits.  Limit: bases of at most 262144 states, else
- * MCD_E_INVALID.  The first call on a device looks up the array's address
- * (make it before any stream capture).  All calls share the array: calls whose
- * work overlaps on the GPU race.  Entries are grouped by row; their order
- * inside a row differs from call to call. */
+ * MCD_E_INVALID.  The first call on a device looks up the array's address and
+ * keeps it (that first call should come before any stream capture; after a
+ * cudaDeviceReset by the application the call is not supported).  All calls
+ * share the array: calls whose work overlaps on the GPU race.  With rows_dev
+ * set and cap < *nnz the call returns MCD_E_INVALID with *nnz set.  Entries
+ * are grouped by row; their order inside a row differs from call to call. */
 int mcd_connections_noalloc(mcd_ctx* ctx, int64_t* rows_dev, int64_t* cols_dev, double* vals_dev,
                             int64_t cap, int64_t* nnz);
 

@@ -133,7 +133,7 @@ int hv_adjoint(mcd_ctx* c, const void* u, const void* v, int ncols, int ld, int 
   const int n = c->n;
   const int nb = c->hp->n_bonds;
   const int nout = nb + 2 * n;
-  const int ctas = 152 * 4;
+  const int ctas = device_sms() * 4;
   cudaStream_t s = c->stream;
   double *part = nullptr, *out = nullptr;
   cudaError_t e = cudaMallocAsync(&part, sizeof(double) * size_t(ctas) * nout * 2, s);

@@ -141,7 +141,7 @@ __global__ void block_combine_kernel(const T* W, T* out, int pw, double beta, co
 
 int grid_for(int64_t work) {
   const int64_t g = (work + kThreads - 1) / kThreads;
-  return int(std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16)));
+  return int(std::max<int64_t>(1, std::min<int64_t>(g, int64_t(device_sms()) * 16)));
 }
 
 // Pivoted Cholesky of the p x p Gram G (row-major): G[piv, piv] = R^T R with
@@ -727,6 +727,7 @@ int one_side(mcd_ctx* c, const std::vector<uint64_t>& kept_w, const std::vector<
   }
   if (st == MCD_OK) {
     st = bl.run(n_blocks, out);
+    if (st == MCD_OK) st = take_wait_errors(sub);   // a product whose bounded wait gave up is incomplete
     if (st != MCD_OK) c->err = sub->err;
   }
   c->launches += sub->launches - before;
@@ -890,7 +891,7 @@ int green_gradient(mcd_ctx* c, const int* site, const int* spin, int L, int n_bl
   gs.ge.assign(n, 0.0);
   gs.gu.assign(n, 0.0);
   double* buf = nullptr;   // d_r [nk] | b, lam, r, p, q, u [N each] | partials [kParts]
-  constexpr int kParts = 152 * 4;
+  const int kParts = device_sms() * 4;
   cudaError_t e = cudaMalloc(&buf, sizeof(double) * (size_t(nk) + 6 * size_t(N) + kParts));
   if (e != cudaSuccess) return fail(c, MCD_E_OOM, "Green gradient: work vectors");
   struct Free {

@@ -345,7 +345,7 @@ __global__ void bcast_kernel(T* out, const double* v, int64_t n, const double* s
     out[k] = T(v[k] * scale_of_inst[inst_of(off, n_inst, k)]);
 }
 
-int egrid(int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>((n + kBT - 1) / kBT, 152 * 16))); }
+int egrid(int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>((n + kBT - 1) / kBT, int64_t(device_sms()) * 16))); }
 
 struct DevPtr {
   void* p = nullptr;
@@ -467,7 +467,7 @@ class Batch {
       a.counter = counter(p);
       cudaError_t e = cudaMemsetAsync(counter(p), 0, sizeof(int), s_);
       if (e != cudaSuccess) return e;
-      const int grid = std::max(1, std::min(nitems_[p], 152 * ctas_per_sm));
+      const int grid = std::max(1, std::min(nitems_[p], device_sms() * ctas_per_sm));
       if (p == 0)
         batch_hv_kernel<T, false, false><<<grid, kBT, smem, s_>>>(a);
       else if (dot)

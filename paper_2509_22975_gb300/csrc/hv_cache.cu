@@ -72,6 +72,7 @@ constexpr int kSStageBytes = kSOffAux2 + kSAux2Bytes;
 static_assert(kSStageBytes % 16 == 0 && kSOffX % 16 == 0 && kSOffAux % 16 == 0 && kSOffAux2 % 16 == 0,
               "stage buffers on 16-byte boundaries");
 constexpr uint32_t kSpinLimit = 1u << 22;    // polls of an mbarrier before a wait gives up
+constexpr uint32_t kTestSpinLimit = 1u << 12;  // the same in a time-out test
 
 // ---- build ------------------------------------------------------------------------
 
@@ -370,9 +371,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0u;
 }
-// waits for the phase of the given parity; false when kSpinLimit polls were not enough
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
+// waits for the phase of the given parity; false when `limit` polls were not enough
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -537,7 +538,7 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
         const int st = int(i % kSStages);
         const CItem it = nxt;
         if (i + 1 < n_my) nxt = a.items[blockIdx.x + (i + 1) * gridDim.x];
-        if (!mbar_wait(&s_empty[st], uint32_t((i / kSStages) & 1) ^ 1u)) {
+        if (!mbar_wait(&s_empty[st], uint32_t((i / kSStages) & 1) ^ 1u, a.spin_limit)) {
           failed = true;
           break;
         }
@@ -575,7 +576,10 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
         const uint32_t bytes = direct ? 0u
                                       : rb + mb + uint32_t(chi - clo) + (x_out ? 0u : uint32_t(xhi - xlo)) +
                                             uint32_t(ahi - alo) + uint32_t(bhi - blo);
-        if (bytes == 0u) {
+        if (blockIdx.x + i * int64_t(gridDim.x) == a.withhold) {
+          // time-out test: no arrival and no copy for this item, so the
+          // waits on its stage run out (nothing is in flight for it)
+        } else if (bytes == 0u) {
           mbar_arrive(&s_full[st]);
         } else {
           mbar_arrive_tx(&s_full[st], bytes);
@@ -600,7 +604,7 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
     // consumers
     for (int64_t i = 0; i < n_my; ++i) {
       const int st = int(i % kSStages);
-      if (!mbar_wait(&s_full[st], uint32_t((i / kSStages) & 1))) {
+      if (!mbar_wait(&s_full[st], uint32_t((i / kSStages) & 1), a.spin_limit)) {
         failed = true;
         break;
       }
@@ -638,7 +642,7 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
     if (warp == SCfg<T>::kCons && lane == 0) {
       // copies still in flight land before the CTA's shared memory is released
       for (int s = 0; s < kSStages; ++s)
-        if (issued[s] >= 0) mbar_wait(&s_full[s], uint32_t((issued[s] / kSStages) & 1));
+        if (issued[s] >= 0) mbar_wait(&s_full[s], uint32_t((issued[s] / kSStages) & 1), a.spin_limit);
     }
     if (threadIdx.x == 0) atomicOr(a.err, 1u);
     __syncthreads();
@@ -936,6 +940,10 @@ cudaError_t launch_stream(mcd_ctx* c, const void* x, void* y, double* partials, 
     a.x_bytes = pass == 0 ? xb_bytes
                           : ((reinterpret_cast<uintptr_t>(x) % 16 == 0) ? (n * int64_t(sizeof(T))) & ~int64_t(15) : 0);
     const bool dot = pass == 1 && partials != nullptr;
+    if (c->wait_test_item >= 0) {
+      a.spin_limit = kTestSpinLimit;
+      if (pass == 1) a.withhold = c->wait_test_item;
+    }
     a.dot_partials = partials;
     a.ticket = ticket;
     a.dot_out = dot_out;
@@ -962,6 +970,7 @@ cudaError_t launch_stream(mcd_ctx* c, const void* x, void* y, double* partials, 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  c->wait_test_item = -1;   // the test option applies to one product
   return cudaSuccess;
 }
 
@@ -1025,6 +1034,20 @@ int cache_errors(mcd_ctx* c, unsigned int* out) {
   if (e != cudaSuccess) return cuda_fail(c, e, "cache error word");
   *out = v | w;
   return MCD_OK;
+}
+
+int take_wait_errors(mcd_ctx* c) {
+  ConnCache& A = c->idx.A.cc;
+  ConnCache& B = c->idx.B.cc;
+  if (!A.err && !B.err) return MCD_OK;
+  unsigned int v = 0;
+  int st = cache_errors(c, &v);
+  if (st != MCD_OK || v == 0) return st;
+  cudaError_t e = cudaSuccess;
+  if (A.err) e = cudaMemsetAsync(A.err, 0, 4, c->stream);
+  if (e == cudaSuccess && B.err) e = cudaMemsetAsync(B.err, 0, 4, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "clear wait-error word");
+  return fail(c, MCD_E_TIMEOUT, "a bounded wait of the streaming H*v kernel gave up; the product is incomplete");
 }
 
 }  // namespace mcd

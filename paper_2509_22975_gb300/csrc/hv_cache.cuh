@@ -78,6 +78,8 @@ struct CArgs {
   unsigned int* ticket;
   double* dot_out;
   unsigned int* err;
+  uint32_t spin_limit;           // polls of an mbarrier before a wait gives up
+  int64_t withhold;              // time-out test: item whose copies are not issued (-1 none)
   // build
   const uint16_t* bond_cls;      // [n_bonds] record class of each bond
   uint16_t* cnt;                 // [n] records of each state
@@ -242,6 +244,8 @@ inline void fill_args(mcd_ctx* c, const Layout& L, CArgs& a) {
   a.clo = cc.clo;
   a.n_cls = cc.n_cls;
   a.err = cc.err;
+  a.spin_limit = 1u << 22;
+  a.withhold = -1;
 }
 
 inline int cls_bytes(mcd_ctx* c) {

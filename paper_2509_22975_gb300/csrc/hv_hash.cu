@@ -790,7 +790,7 @@ cudaError_t launch_hash1(mcd_ctx* c, const void* x, void* y, int ld, double* par
     cudaFuncSetAttribute(hv_hash1_kernel<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     configured = int(smem);
   }
-  const int cap = 152 * 32;
+  const int cap = device_sms() * 32;
   for (int pass = 0; pass < 2; ++pass) {
     const Layout& L = pass ? c->idx.A : c->idx.B;
     a.L = L;
@@ -827,7 +827,7 @@ cudaError_t launch_hashm(mcd_ctx* c, const void* x, void* y, int ncols, int ld) 
     cudaFuncSetAttribute(hv_hashm_kernel<T, VEC, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     configured = int(smem);
   }
-  const int cap = 152 * 32;
+  const int cap = device_sms() * 32;
   for (int pass = 0; pass < 2; ++pass) {
     const Layout& L = pass ? c->idx.A : c->idx.B;
     a.L = L;

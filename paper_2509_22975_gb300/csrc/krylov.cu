@@ -236,7 +236,7 @@ __global__ void scale_kernel(T* v, int64_t n, double f) {
 
 int vec_grid(int64_t n) {
   const int64_t g = (n + 4 * kThreads - 1) / (4 * kThreads);
-  return int(std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8)));
+  return int(std::max<int64_t>(1, std::min<int64_t>(g, int64_t(device_sms()) * 8)));
 }
 
 int ensure_work(mcd_ctx* c, int dtype, int max_iter) {
@@ -244,7 +244,7 @@ int ensure_work(mcd_ctx* c, int dtype, int max_iter) {
   const int64_t n = c->idx.n;
   const size_t es = dtype == MCD_F64 ? 8 : 4;
   const int cap = max_iter + 2;
-  const int ctas = std::max<int>(int(c->idx.A.n_items), 152 * 8) + 8;
+  const int ctas = std::max<int>(int(c->idx.A.n_items), device_sms() * 8) + 8;
   // keep every Krylov vector when it fits in half of the free memory (no
   // second pass for the Ritz vector); else two rotating slots
   size_t free_b = 0, total_b = 0;
@@ -336,6 +336,10 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
       e = cudaMemcpyAsync(dot.data(), w.scal + sl.dot(0), sizeof(double) * m, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(c, e, "Lanczos read-back");
+    {
+      const int ws = take_wait_errors(c);   // a product whose bounded wait gave up is incomplete
+      if (ws != MCD_OK) return ws;
+    }
     // coefficients a_n = dot_n / nrm2_n, b_n = sqrt(nrm2_n) (n >= 1)
     a.assign(m, 0.0);
     b.assign(m + 1, 0.0);
@@ -425,6 +429,10 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
   e = cudaMemcpyAsync(&rr, w.scal + sl.misc(2), 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "Ritz residual");
+  {
+    const int ws = take_wait_errors(c);
+    if (ws != MCD_OK) return ws;
+  }
   *resid_out = std::sqrt(rr / nn);
   // keep the normalised ground state for the Green function
   if (!c->gs_psi || c->gs_n != n) {

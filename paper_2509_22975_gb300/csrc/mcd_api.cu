@@ -2,6 +2,7 @@
 // handling and dispatch to the sampler, index, H*v and Lanczos code.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -17,6 +18,21 @@ int fail(mcd_ctx* c, int status, const std::string& msg) {
 
 int cuda_fail(mcd_ctx* c, cudaError_t e, const char* where) {
   return fail(c, MCD_E_CUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+int device_sms() {
+  constexpr int kDevs = 64;
+  static std::atomic<int> cached[kDevs] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  if (dev < kDevs) {
+    const int v = cached[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+  if (dev < kDevs) cached[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 }  // namespace mcd
@@ -166,6 +182,14 @@ int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
     case MCD_OPT_SAMPLER_DEVICE:
       if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "SAMPLER_DEVICE must be 0, 1 or 2");
       c->sampler_where = int(value);
+      return MCD_OK;
+    case MCD_OPT_APPLY_SYNC:
+      if (value < 0 || value > 1) return fail(c, MCD_E_INVALID, "APPLY_SYNC must be 0 or 1");
+      c->apply_sync = int(value);
+      return MCD_OK;
+    case MCD_OPT_WAIT_TEST:
+      if (value < -1) return fail(c, MCD_E_INVALID, "WAIT_TEST must be -1 or an item index");
+      c->wait_test_item = value;
       return MCD_OK;
     case MCD_OPT_HV_CACHE:
       if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "HV_CACHE must be 0, 1 or 2");
@@ -578,7 +602,9 @@ int mcd_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype) 
   const uintptr_t bytes = uintptr_t(c->idx.n) * uintptr_t(ld) * es;
   if (xa < ya + bytes && ya < xa + bytes) return fail(c, MCD_E_INVALID, "x and y overlap");
   if (xa % es || ya % es) return fail(c, MCD_E_INVALID, "misaligned vector");
-  return hv_apply(c, x, y, ncols, ld, dtype, nullptr, 0);
+  st = hv_apply(c, x, y, ncols, ld, dtype, nullptr, 0);
+  if (st != MCD_OK || !c->apply_sync) return st;
+  return take_wait_errors(c);
 }
 
 int mcd_hv_adjoint(mcd_ctx* c, const void* u, const void* v, int ncols, int ld, int dtype, double* grad_t,

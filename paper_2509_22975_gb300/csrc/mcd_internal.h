@@ -226,10 +226,15 @@ struct mcd_ctx {
   int sampler_threads = 0;
   int sampler_where = 0;                // 0 auto, 1 host threads, 2 device
   int hv_cache = 0;                     // 0 auto, 1 off, 2 required
+  int apply_sync = 1;                   // mcd_apply waits and reads the wait-error words
+  int64_t wait_test_item = -1;          // one-shot: withhold this item's copies (time-out test)
   mcd::Timing* tm = nullptr;
 };
 
 namespace mcd {
+
+// streaming multiprocessors of the current device (queried once per device)
+int device_sms();
 
 // error helpers (mcd_api.cu)
 int fail(mcd_ctx* c, int status, const std::string& msg);
@@ -302,6 +307,9 @@ void cache_invalidate(Layout& L);
 void free_cache(Layout& L);
 // *out = 1 when a bounded wait of a cached kernel gave up since the records were built
 int cache_errors(mcd_ctx* c, unsigned int* out);
+// MCD_E_TIMEOUT (and the words cleared) when a bounded wait gave up since the
+// last check, else MCD_OK; synchronizes the context's stream
+int take_wait_errors(mcd_ctx* c);
 // cached H*V for many columns, or one column with a row stride (hv_cache_cols.cu);
 // *used = false when the columns' layout is not covered (the caller falls back)
 cudaError_t cache_apply_cols(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, bool* used);

@@ -4,11 +4,9 @@
 // mcd_connections needs per-row counts and offsets and takes them from the
 // stream-ordered allocator on every call.  Some callers cannot allow that:
 // an application that hands all device memory to its own pool at start-up
-// and forbids any later allocation by a library, a caller that runs under a
-// fixed memory budget where a late allocation can fail, or one that records
-// its work into a CUDA graph, where an allocation either breaks the capture
-// or adds allocation nodes the graph owner did not plan for.  This variant
-// keeps its scratch in one fixed array in device global memory instead:
+// and forbids any later allocation by a library, or a caller that runs under
+// a fixed memory budget where a late allocation can fail.  This variant keeps
+// its scratch in one fixed array in device global memory instead:
 //
 //   g_noalloc_scratch: kNoAllocMaxStates per-row counts, kNoAllocMaxStates
 //   per-row offsets (reused as write cursors) and the total, 2 MiB in all.
@@ -17,10 +15,13 @@
 //
 // Host code cannot use the array's name as a device address, so the first
 // call on each device (with that device current) looks the address up with
-// cudaGetSymbolAddress and keeps it; make that first call before any stream
-// capture.  Every call reuses the same array and leaves its contents behind:
-// the counts are cleared at the start of each call, and calls whose work
-// overlaps on the GPU (two streams, or two contexts on one device) race on it.
+// cudaGetSymbolAddress and keeps it for the life of the process; that first
+// call should come before any stream capture.  The kept address belongs to
+// the device's primary context: after the application resets the device
+// (cudaDeviceReset), calls of this entry point are not supported.  Every call
+// reuses the same array and leaves its contents behind: the counts are
+// cleared at the start of each call, and calls whose work overlaps on the GPU
+// (two streams, or two contexts on one device) race on it.
 #include <mutex>
 
 #include "mcd_internal.h"
@@ -165,6 +166,7 @@ extern "C" int mcd_connections_noalloc(mcd_ctx* c, int64_t* rows, int64_t* cols,
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "no-alloc connection count");
   *nnz = int64_t(total);
+  c->idx.nnz = int64_t(total);
   if (!rows) return MCD_OK;
   if (int64_t(total) > cap) return fail(c, MCD_E_INVALID, "connections: capacity too small");
   na_conn_kernel<false><<<grid_of(n, kThreads), kThreads, 0, s>>>(c->idx.B, *c->hp, nullptr, off, rows, cols,

@@ -385,7 +385,7 @@ int sample_basis_device(mcd_ctx* c, uint64_t seed, int64_t n_target, double beta
         e = ds.alloc(tot, 8);
         if (e == cudaSuccess) e = cudaMemsetAsync(tot.p, 0, 8, s);
         if (e == cudaSuccess) {
-          sum_counts64_kernel<<<152 * 4, kT, 0, s>>>(cnt.as<uint32_t>(), nfr, tot.as<unsigned long long>());
+          sum_counts64_kernel<<<device_sms() * 4, kT, 0, s>>>(cnt.as<uint32_t>(), nfr, tot.as<unsigned long long>());
           MCD_LAUNCHED(c);
           e = cudaMemcpyAsync(&h, tot.p, 8, cudaMemcpyDeviceToHost, s);
         }
