@@ -102,6 +102,14 @@ typedef enum { MCD_F64 = 0, MCD_F32 = 1 } mcd_dtype;
                                    wait only 4096 times, so that the waits on
                                    that item give up; -1 = off (default).
                                    Applies to one product, then resets. */
+#define MCD_OPT_KRYLOV_STORE 9   /* Lanczos vectors of mcd_lanczos_ground:
+                                   0 = kept in device memory when they fit in
+                                   half of the free memory, else regenerated
+                                   (default); 1 = always regenerated: two
+                                   rotating slots, and a second pass of the
+                                   recursion (same fixed-order reductions, so
+                                   the same vectors bit for bit) forms the
+                                   Ritz vector. */
 #define MCD_OPT_HASH_ITEM 4     /* states per work item of the hash-lookup
                                    kernels: a power of two in [64, 4096]
                                    (default 1024).  Blocks of more states are

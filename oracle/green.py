@@ -78,33 +78,35 @@ def block_krylov(apply, Phi: np.ndarray, n_blocks: int, dtol: float = 1e-10):
     H_eff = V^T H V.  Each candidate is orthogonalised against every earlier
     basis vector (classical Gram-Schmidt, twice) and dropped ("deflated") when
     its remaining norm is below dtol times its norm before."""
-    N = Phi.shape[0]
-    V = np.zeros((N, 0))
+    N, L = Phi.shape
+    # storage for at most L vectors per block; columns [0, k) hold the basis
+    V = np.zeros((N, max(L * max(n_blocks, 1), 1)), order="F")
+    k = 0
 
     def extend(cands):
-        nonlocal V
-        added = []
+        nonlocal k
+        k0 = k
         for v in np.asarray(cands).T:
             v = np.array(v, dtype=np.float64)
             n0 = np.linalg.norm(v)
             for _ in range(2):
-                B = np.column_stack([V] + added) if added else V
+                B = V[:, :k]
                 v = v - B @ (B.T @ v)
             nv = np.linalg.norm(v)
             if nv > dtol * max(n0, 1e-300):
-                added.append(v / nv)
-        blk = np.column_stack(added) if added else np.zeros((N, 0))
-        V = np.column_stack([V, blk])
-        return blk
+                V[:, k] = v / nv
+                k += 1
+        return V[:, k0:k]
 
     blk = extend(Phi)
     for _ in range(1, n_blocks):
         if blk.shape[1] == 0:
             break
         blk = extend(np.column_stack([apply(blk[:, j]) for j in range(blk.shape[1])]))
-    HV = np.column_stack([apply(V[:, j]) for j in range(V.shape[1])]) if V.shape[1] else V
-    Heff = V.T @ HV
-    return V, 0.5 * (Heff + Heff.T)
+    Vk = V[:, :k]
+    HV = np.column_stack([apply(Vk[:, j]) for j in range(k)]) if k else Vk
+    Heff = Vk.T @ HV
+    return Vk, 0.5 * (Heff + Heff.T)
 
 
 @dataclass

@@ -22,7 +22,7 @@ MCD_SAMPLE_NEW_ONLY = 1
 MCD_OPT_HV_ALGO, MCD_OPT_KERNEL_TIMING, MCD_OPT_SAMPLER_THREADS, MCD_OPT_HASH_ITEM = 1, 2, 3, 4
 MCD_OPT_SAMPLER_DEVICE = 5
 MCD_OPT_HV_CACHE = 6
-MCD_OPT_APPLY_SYNC, MCD_OPT_WAIT_TEST = 7, 8
+MCD_OPT_APPLY_SYNC, MCD_OPT_WAIT_TEST, MCD_OPT_KRYLOV_STORE = 7, 8, 9
 MCD_E_TIMEOUT = -7
 CACHE_AUTO, CACHE_OFF, CACHE_REQUIRED = 0, 1, 2
 SAMPLER_AUTO, SAMPLER_HOST, SAMPLER_DEVICE = 0, 1, 2

@@ -250,7 +250,8 @@ int ensure_work(mcd_ctx* c, int dtype, int max_iter) {
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   const size_t held = w.V ? size_t(w.nvec) * size_t(w.ld) * (w.dtype == MCD_F64 ? 8 : 4) : 0;
-  const bool want_store = double(max_iter + 1) * double(n) * double(es) <= 0.5 * double(free_b + held);
+  const bool want_store = c->krylov_store == 0 &&
+                          double(max_iter + 1) * double(n) * double(es) <= 0.5 * double(free_b + held);
   const int nvec = want_store ? max_iter + 1 : 2;
   if (w.n == n && w.dtype == dtype && w.scal_cap >= cap && w.max_ctas >= ctas && w.nvec >= nvec &&
       w.stored == want_store)

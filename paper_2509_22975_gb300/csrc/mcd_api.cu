@@ -183,6 +183,10 @@ int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
       if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "SAMPLER_DEVICE must be 0, 1 or 2");
       c->sampler_where = int(value);
       return MCD_OK;
+    case MCD_OPT_KRYLOV_STORE:
+      if (value < 0 || value > 1) return fail(c, MCD_E_INVALID, "KRYLOV_STORE must be 0 or 1");
+      c->krylov_store = int(value);
+      return MCD_OK;
     case MCD_OPT_APPLY_SYNC:
       if (value < 0 || value > 1) return fail(c, MCD_E_INVALID, "APPLY_SYNC must be 0 or 1");
       c->apply_sync = int(value);

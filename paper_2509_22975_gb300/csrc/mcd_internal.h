@@ -226,6 +226,7 @@ struct mcd_ctx {
   int sampler_threads = 0;
   int sampler_where = 0;                // 0 auto, 1 host threads, 2 device
   int hv_cache = 0;                     // 0 auto, 1 off, 2 required
+  int krylov_store = 0;                 // 0 auto, 1 always regenerate the Lanczos vectors
   int apply_sync = 1;                   // mcd_apply waits and reads the wait-error words
   int64_t wait_test_item = -1;          // one-shot: withhold this item's copies (time-out test)
   mcd::Timing* tm = nullptr;

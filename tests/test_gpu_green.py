@@ -1,8 +1,11 @@
 """GPU band-Lanczos Green function through the C ABI against the oracle's
-block-Krylov projection: same truncation, excited spaces and Krylov space,
-so G(z) agrees; the anticommutator sum rule through the 1/z tail; the dense
-Lehmann sum once the Krylov space is exhausted; fp32 vectors; argument and
-state errors; the 12-site configuration at full size."""
+block-Krylov projection from the oracle's own ground state: same truncation
+(w_t = 1, or w_t inside a gap between weights), excited spaces and Krylov
+space, so G(z) agrees; the 12-site workload's 150 blocks on a nested prefix
+of its basis against stored oracle values; fp32 vectors (and the fp32 ground
+state) against the oracle; the anticommutator sum rule through the 1/z tail;
+the dense Lehmann sum once the Krylov space is exhausted; argument and state
+errors; the 12-site configuration at full size."""
 import numpy as np
 import pytest
 import torch
@@ -35,8 +38,22 @@ def gpu_ground(ctx, n, dtype=pkg.MCD_F64):
     return r, psi.double().cpu().numpy()
 
 
-@pytest.mark.parametrize("w_t,n_blocks", [(1.0, 8), (1.0, 25), (0.95, 12)])
+def gap_w_t(psi, near):
+    """A target weight inside a gap between distinct weights of psi, at or
+    above `near` (the kept set is then the same for the device's and the
+    oracle's ground states, which agree far below the gap)."""
+    p = np.sort((psi / np.linalg.norm(psi)) ** 2)[::-1]
+    cum = np.cumsum(p)
+    k0 = max(int(np.searchsorted(cum, near * cum[-1])), 1)
+    k = next(k for k in range(k0, len(p) - 1) if p[k] > 1.001 * p[k + 1])
+    return float((cum[k - 1] + 0.5 * p[k]) / cum[-1])
+
+
+@pytest.mark.parametrize("w_t,n_blocks", [(1.0, 8), (1.0, 25), ("gap0.95", 12), ("gap0.999", 30)])
 def test_matches_oracle_block_krylov(w_t, n_blocks):
+    # the oracle works from its own dense ground state (not the device's):
+    # truncation, F~+-, start vectors and the block Krylov space all follow
+    # from an independently computed Omega~ (G is even in the sign of Omega~)
     w = ring8_half_filled()
     ctx = device_ctx(w)
     B = ctx.mcd_get_basis()
@@ -44,11 +61,12 @@ def test_matches_oracle_block_krylov(w_t, n_blocks):
     M = model(w)
     E_ref, v_ref, _ = LZ.dense_ground(H.build(M, B).dense())
     assert abs(r["E0"] - E_ref) < 1e-11 * abs(E_ref)
+    if isinstance(w_t, str):
+        w_t = gap_w_t(v_ref, float(w_t[3:]))
     orb = [(i, 0) for i in range(8)]
     z = np.linspace(-8, 8, 17) + 0.25j
     Gg, dp, dm = ctx.mcd_band_lanczos_green(orb, n_blocks, w_t, z)
-    # the oracle takes the device's ground state, so both truncate the same weights
-    ref = G.green(M, B, psi, r["E0"], orb, n_blocks, w_t, z)
+    ref = G.green(M, B, v_ref, E_ref, orb, n_blocks, w_t, z)
     assert dp == ref.plus.dim and dm == ref.minus.dim
     scale = np.max(np.abs(ref.G))
     assert np.max(np.abs(Gg - ref.G)) < 1e-7 * scale, np.max(np.abs(Gg - ref.G)) / scale
@@ -76,16 +94,61 @@ def test_exhausted_krylov_and_sum_rule():
     assert np.max(np.abs(A - A[::-1])) < 1e-8 * np.max(A)    # particle-hole symmetry
 
 
-def test_fp32_vectors():
+@pytest.mark.parametrize("ground_dtype", [pkg.MCD_F64, pkg.MCD_F32])
+def test_fp32_vectors_against_the_oracle(ground_dtype):
+    # fp32 Krylov vectors (fp64 Gram-Schmidt and coefficients) against the
+    # oracle's fp64 G from its own dense ground state; with the fp32 ground
+    # state too (the whole fp32 form): E0 within 1e-6 and G within 1e-4 of
+    # the largest |G| (the fp32 Ritz vector carries ~1e-4 relative error)
     w = ring8_half_filled()
     ctx = device_ctx(w)
     B = ctx.mcd_get_basis()
-    r, psi = gpu_ground(ctx, len(B))
+    r, psi = gpu_ground(ctx, len(B), ground_dtype)
+    M = model(w)
+    E_ref, v_ref, _ = LZ.dense_ground(H.build(M, B).dense())
+    assert abs(r["E0"] - E_ref) < (1e-6 if ground_dtype == pkg.MCD_F32 else 1e-11 * abs(E_ref))
     orb = [(i, 0) for i in range(8)]
     z = np.linspace(-8, 8, 17) + 0.25j
-    G64, _, _ = ctx.mcd_band_lanczos_green(orb, 20, 1.0, z, dtype=pkg.MCD_F64)
-    G32, _, _ = ctx.mcd_band_lanczos_green(orb, 20, 1.0, z, dtype=pkg.MCD_F32)
-    assert np.max(np.abs(G32 - G64)) < 1e-4 * np.max(np.abs(G64))
+    G32, dp, dm = ctx.mcd_band_lanczos_green(orb, 20, 1.0, z, dtype=pkg.MCD_F32)
+    ref = G.green(M, B, v_ref, E_ref, orb, 20, 1.0, z)
+    assert dp == ref.plus.dim and dm == ref.minus.dim
+    err = np.max(np.abs(G32 - ref.G)) / np.max(np.abs(ref.G))
+    print(f"fp32 G vs oracle (ground state {'fp32' if ground_dtype else 'fp64'}): {err:.3e}, "
+          f"|dE0| = {abs(r['E0'] - E_ref):.3e}")
+    assert err < 1e-4
+
+
+def tilted12_prefix_golden():
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", "green_tilted12_prefix.json")))
+
+
+@pytest.mark.parametrize("dtype,tol", [(pkg.MCD_F64, 1e-7), (pkg.MCD_F32, 1e-4)])
+def test_tilted12_prefix_150_blocks_matches_oracle(dtype, tol):
+    # the 12-site Green-function workload (12 spin-up orbitals, 150 blocks,
+    # w_t in the gap nearest above 0.999) on the nested 2e4-state prefix of its
+    # Monte Carlo basis, against the oracle's G(i omega_n) at beta_M = 50,
+    # n = 0..63 (stored by tests/golden/make_golden.py from the oracle's own
+    # Lanczos ground state and block Krylov space, full reorthogonalisation)
+    gold = tilted12_prefix_golden()
+    w = C.tilted12_u8()
+    w.mu = w.U / 2
+    ctx = device_ctx(w, nf=gold["n_f"])
+    n = ctx.mcd_basis_info(nnz=False)["n_states"]
+    assert n == gold["n_basis"]
+    r, _ = gpu_ground(ctx, n, dtype)
+    assert abs(r["E0"] - gold["E0"]) < (1e-6 if dtype == pkg.MCD_F32 else 1e-10 * abs(gold["E0"]))
+    wn = (2 * np.arange(gold["n_matsubara"]) + 1) * np.pi / gold["beta_M"]
+    orb = [(i, 0) for i in range(12)]
+    Gg, dp, dm = ctx.mcd_band_lanczos_green(orb, gold["n_blocks"], gold["w_t"], 1j * wn, dtype=dtype)
+    assert dp == gold["dim_plus"] and dm == gold["dim_minus"]
+    ref = np.asarray(gold["G_diag_re"]) + 1j * np.asarray(gold["G_diag_im"])
+    got = np.einsum("zaa->za", Gg)
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    print(f"tilted12 prefix, {'fp32' if dtype else 'fp64'}: max |G - G_oracle| / max |G_oracle| = {err:.3e}, "
+          f"|dE0| = {abs(r['E0'] - gold['E0']):.3e}")
+    assert err < tol
 
 
 def test_spin_down_orbitals_and_errors():

@@ -167,3 +167,27 @@ def test_bases_of_every_size_mod_four(nf, dtype):
     r = ctx.mcd_lanczos_ground(800, 1e-12 if dtype == pkg.MCD_F64 else 1e-8, 0, dtype, psi=psi,
                                allow_not_converged=dtype == pkg.MCD_F32)
     assert abs(r["E0"] - E_ref) <= (1e-10 * abs(E_ref) if dtype == pkg.MCD_F64 else 1e-6)
+
+
+@pytest.mark.parametrize("name,nf,dtype", [("ring8", 2000, pkg.MCD_F64), ("tilted12", 1 << 16, pkg.MCD_F64),
+                                           ("tilted12", 1 << 16, pkg.MCD_F32)])
+def test_regenerated_krylov_vectors_match_stored(name, nf, dtype):
+    # MCD_OPT_KRYLOV_STORE = 1 keeps two rotating slots and forms the Ritz
+    # vector in a second pass of the recursion; every reduction has a fixed
+    # order, so the second pass regenerates the same vectors and the Ritz
+    # vector is the same sum in the same order: equal bit for bit to the
+    # stored-vector run (fp64 and fp32 vectors alike)
+    w = C.WORKLOADS[name]()
+    ctx = device_ctx(w, nf=nf)
+    n = ctx.mcd_basis_info(nnz=False)["n_states"]
+    tdt = torch.float64 if dtype == pkg.MCD_F64 else torch.float32
+    out = {}
+    for store in (0, 1):
+        ctx.mcd_set_option(pkg.MCD_OPT_KRYLOV_STORE, store)
+        psi = torch.empty(n, dtype=tdt, device=DEV)
+        r = ctx.mcd_lanczos_ground(120, 0.0, 3, dtype, psi=psi)
+        out[store] = (r, psi.cpu().numpy())
+    (r0, p0), (r1, p1) = out[0], out[1]
+    assert r0["iters"] == r1["iters"] == 120
+    assert r0["E0"] == r1["E0"] and r0["residual"] == r1["residual"]
+    assert np.array_equal(p0, p1)

@@ -49,6 +49,20 @@ def test_device_equals_oracle():
     assert np.array_equal(Bd, Bo)
 
 
+@pytest.mark.parametrize("name,nf", [("rect24_u8", 30000), ("rect24_u8", 120000), ("square16_u8", 100000)])
+@pytest.mark.parametrize("flags", [0, pkg.MCD_SAMPLE_NEW_ONLY])
+def test_device_and_host_equal_oracle_beyond_16_sites(name, nf, flags):
+    # the 24-site cluster (words above 32 bits, n > 16 sites) and the 4x4 one:
+    # both library samplers against the oracle, word for word
+    w = getattr(C, name)()
+    Bo = S.sample_basis(w.n_sites, w.lat.t, w.U_sites, w.n_up, w.n_dn, nf, w.beta, [w.seed_word()], seed=w.seed,
+                        flags=flags)
+    for where in (pkg.SAMPLER_DEVICE, pkg.SAMPLER_HOST):
+        B, st = sample(w, nf, where, flags)
+        assert st == 0 and len(B) == nf
+        assert np.array_equal(B, Bo)
+
+
 def test_overshoot_and_nesting():
     # every size cuts some step short: the device keeps the same states of
     # smallest priority as the host, and smaller bases are prefixes in set terms
