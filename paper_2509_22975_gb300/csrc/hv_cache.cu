@@ -71,8 +71,6 @@ constexpr int kSOffAux2 = kSOffAux + kSAuxBytes;
 constexpr int kSStageBytes = kSOffAux2 + kSAux2Bytes;
 static_assert(kSStageBytes % 16 == 0 && kSOffX % 16 == 0 && kSOffAux % 16 == 0 && kSOffAux2 % 16 == 0,
               "stage buffers on 16-byte boundaries");
-constexpr uint32_t kSpinLimit = 1u << 22;    // polls of an mbarrier before a wait gives up
-constexpr uint32_t kTestSpinLimit = 1u << 12;  // the same in a time-out test
 
 // ---- build ------------------------------------------------------------------------
 
@@ -342,48 +340,6 @@ __global__ void item_groups_kernel(CItem* items, int64_t n_items, const uint32_t
 }
 
 // ---- apply --------------------------------------------------------------------------
-
-// ---- mbarrier and bulk copy (PTX) -----------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0u;
-}
-// waits for the phase of the given parity; false when `limit` polls were not enough
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t i = 0; i < limit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-// global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
 
 // One item of the streaming kernel, for the calling consumer warp: its
 // slices warp, warp + kCons, ...  colp = slice offsets from the item's first
@@ -737,6 +693,9 @@ int build_layout(mcd_ctx* c, Layout& L, const LayoutItems& li, const std::vector
   cc.n_items = int64_t(li.items.size());
   cc.n_slices = n_slices;
   cc.max_stage = li.max_stage;
+  cc.stage_rows.resize(li.items.size());
+  for (size_t i = 0; i < li.items.size(); ++i) cc.stage_rows[i] = li.items[i].se - li.items[i].sb;
+  cc.units_key = -1;
   cc.n_cls = int(coef.size());
   const int nc1 = std::max(cc.n_cls, 1);
   cudaError_t e = grow(cc.items, cc.items_cap, cc.n_items, sizeof(CItem), s);
@@ -999,7 +958,7 @@ void cache_invalidate(Layout& L) {
 void free_cache(Layout& L) {
   ConnCache& cc = L.cc;
   auto f = [](void* p) { if (p) cudaFree(p); };
-  f(cc.items); f(cc.col); f(cc.smap); f(cc.rec); f(cc.c64); f(cc.xb); f(cc.yb); f(cc.xbm);
+  f(cc.items); f(cc.col); f(cc.smap); f(cc.rec); f(cc.c64); f(cc.xb); f(cc.yb); f(cc.xbm); f(cc.units);
   cc = ConnCache();
 }
 

@@ -18,6 +18,8 @@ constexpr uint16_t kNoState = 0xFFFFu;
 constexpr int kBuildStageWords = 12288;      // minor words staged by the build kernels (48 KiB)
 constexpr int kMStageBytes = 48 * 1024;      // staged x rows of the multi-column kernel
 constexpr int kMaxCount = 512;               // records of one state in one pass (n_bonds <= 496)
+constexpr uint32_t kSpinLimit = 1u << 22;    // polls of an mbarrier before a wait gives up
+constexpr uint32_t kTestSpinLimit = 1u << 12;  // the same in a time-out test (MCD_OPT_WAIT_TEST)
 
 template <typename R>
 struct Rec;
@@ -78,6 +80,8 @@ struct CArgs {
   unsigned int* ticket;
   double* dot_out;
   unsigned int* err;
+  const uint2* units;            // many-column kernel: {item, col0 | G << 16 | x in global memory << 24}
+  int64_t n_units;
   uint32_t spin_limit;           // polls of an mbarrier before a wait gives up
   int64_t withhold;              // time-out test: item whose copies are not issued (-1 none)
   // build
@@ -208,6 +212,58 @@ __device__ __forceinline__ Coef<T> diag_of(const HamParams& hp, const float* dhi
   return diag_coef<T>(hp, up, dn);
 }
 
+// ---- mbarrier and bulk copy (PTX) -----------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// waits for the phase of the given parity; false when `limit` polls were not enough
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned), L2 only
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// one arrival on bar once every cp.async this thread issued so far has landed
+// (counts toward the barrier's expected arrivals)
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // ---- host ------------------------------------------------------------------------
 
 // (re)allocates p to at least need bytes, stream-ordered
@@ -244,7 +300,7 @@ inline void fill_args(mcd_ctx* c, const Layout& L, CArgs& a) {
   a.clo = cc.clo;
   a.n_cls = cc.n_cls;
   a.err = cc.err;
-  a.spin_limit = 1u << 22;
+  a.spin_limit = kSpinLimit;
   a.withhold = -1;
 }
 

@@ -132,6 +132,12 @@ struct ConnCache {
   void* yb = nullptr;            // pass B's part of y (streaming kernels), read by pass A
   unsigned int* err = nullptr;   // set by a kernel whose bounded wait ran out
   int64_t items_cap = 0, col_cap = 0, smap_cap = 0, rec_cap = 0, cls_cap = 0, xb_cap = 0, yb_cap = 0, xbm_cap = 0;
+  // many-column kernel: stage rows (se - sb) of each item (host), and the work
+  // units (item, column tile) of the last column count and element size
+  std::vector<uint32_t> stage_rows;
+  uint2* units = nullptr;
+  int64_t n_units = 0, units_cap = 0;
+  int units_key = -1;            // ncp * 16 + element size of `units` (-1 none)
 };
 
 struct Layout {

@@ -98,8 +98,9 @@ def test_exhausted_krylov_and_sum_rule():
 def test_fp32_vectors_against_the_oracle(ground_dtype):
     # fp32 Krylov vectors (fp64 Gram-Schmidt and coefficients) against the
     # oracle's fp64 G from its own dense ground state; with the fp32 ground
-    # state too (the whole fp32 form): E0 within 1e-6 and G within 1e-4 of
-    # the largest |G| (the fp32 Ritz vector carries ~1e-4 relative error)
+    # state too (the whole fp32 form): E0 within 1e-6 and G within 1e-5 of
+    # the largest |G| (measured 2e-7 and 4e-7: fp32 rounding of the Krylov
+    # vectors, u = 6e-8, grown by the recursion)
     w = ring8_half_filled()
     ctx = device_ctx(w)
     B = ctx.mcd_get_basis()
@@ -115,7 +116,7 @@ def test_fp32_vectors_against_the_oracle(ground_dtype):
     err = np.max(np.abs(G32 - ref.G)) / np.max(np.abs(ref.G))
     print(f"fp32 G vs oracle (ground state {'fp32' if ground_dtype else 'fp64'}): {err:.3e}, "
           f"|dE0| = {abs(r['E0'] - E_ref):.3e}")
-    assert err < 1e-4
+    assert err < 1e-5
 
 
 def tilted12_prefix_golden():
@@ -124,7 +125,7 @@ def tilted12_prefix_golden():
     return json.load(open(os.path.join(os.path.dirname(__file__), "golden", "green_tilted12_prefix.json")))
 
 
-@pytest.mark.parametrize("dtype,tol", [(pkg.MCD_F64, 1e-7), (pkg.MCD_F32, 1e-4)])
+@pytest.mark.parametrize("dtype,tol", [(pkg.MCD_F64, 1e-10), (pkg.MCD_F32, 1e-5)])
 def test_tilted12_prefix_150_blocks_matches_oracle(dtype, tol):
     # the 12-site Green-function workload (12 spin-up orbitals, 150 blocks,
     # w_t in the gap nearest above 0.999) on the nested 2e4-state prefix of its
