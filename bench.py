@@ -388,6 +388,91 @@ def rect24_hv(pkg, configs, dev, peak, cols=(1, 24, 48), reps=5):
     return res
 
 
+def band_green(pkg, configs, dev, peak, name, n_f, n_blocks, w_t=0.999, f32=True, mu_half=True, n_mats=64,
+               beta_m=50.0):
+    """Band-Lanczos Green function end to end (App. C): Monte Carlo basis,
+    Lanczos ground state, target-weight truncation, excited spaces F~+- of the
+    spin-up orbitals of every site, the start blocks and n_blocks band steps in
+    each space, G(i omega_n) on n_mats Matsubara points at beta_M.  Wall time of
+    the Green-function call, and the H~V share from per-kernel CUDA events."""
+    import numpy as np
+    import torch
+    w = getattr(configs, name)()
+    if mu_half:
+        w.mu = w.U / 2
+    ctx = pkg.Context(dev.index or 0)
+    ctx.mcd_set_hamiltonian(w.lat.t, w.eps, w.U, w.n_up, w.n_dn)
+    ctx.mcd_build_basis(w.seed, n_f, w.beta, [w.seed_word()])
+    n = ctx.mcd_basis_info(nnz=False)["n_states"]
+    dt = pkg.MCD_F32 if f32 else pkg.MCD_F64
+    psi = torch.empty(n, dtype=torch.float32 if f32 else torch.float64, device=dev)   # the kept ground state
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = ctx.mcd_lanczos_ground(800, 1e-7 if f32 else 1e-12, 0, dt, psi=psi, allow_not_converged=True)
+    torch.cuda.synchronize()
+    t_gs = time.perf_counter() - t0
+    del psi
+    orb = [(i, 0) for i in range(w.n_sites)]
+    z = 1j * (2 * np.arange(n_mats) + 1) * np.pi / beta_m
+    ctx.mcd_set_option(pkg.MCD_OPT_KERNEL_TIMING, 1)
+    ctx.mcd_kernel_times(reset=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G, dp, dm = ctx.mcd_band_lanczos_green(orb, n_blocks, w_t, z, dtype=dt)
+    torch.cuda.synchronize()
+    t_g = time.perf_counter() - t0
+    kms, kcnt = ctx.mcd_kernel_times(reset=True)
+    ctx.mcd_set_option(pkg.MCD_OPT_KERNEL_TIMING, 0)
+    s = 4 if f32 else 8
+    L_ = len(orb)
+    hv_ms = kms[0] + kms[1]
+    hv_bytes = n_blocks * (dp + dm) * (8 + 2 * L_ * s)   # every block taken as L columns wide
+    tail = float(np.max(np.abs(z[-1] * G[-1] - np.eye(L_))))
+    out = {"workload": f"{name} mu={'U/2' if mu_half else 0} MC basis {n} states, {L_} spin-up orbitals x 2 "
+                       f"(c^dag, c), {n_blocks} band blocks per space, w_t {w_t}, G(i w_n) n<{n_mats} "
+                       f"beta_M {beta_m}",
+           "dtype": "f32 vectors, f64 Gram-Schmidt" if f32 else "f64", "n_states": n, "E0": r["E0"],
+           "lanczos_iters": r["iters"], "ground_state_s": t_gs, "dim_plus": dp, "dim_minus": dm,
+           "green_s": t_g, "blocks_per_s": 2 * n_blocks / t_g,
+           "hv_ms": hv_ms, "hv_launches": int(kcnt[0] + kcnt[1]), "hv_share": hv_ms * 1e-3 / t_g,
+           "hv_algorithmic_GBps": hv_bytes / (hv_ms * 1e-3) / 1e9 if hv_ms > 0 else None,
+           "hv_frac_of_peak": hv_bytes / (hv_ms * 1e-3) / 1e9 / peak if hv_ms > 0 else None,
+           "max_abs_zG_minus_1_at_largest_w_n": tail}
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def green_precision(pkg, configs, dev):
+    """The 12-site Green-function workload on the 2e4-state prefix of its
+    basis in fp32 and fp64 against stored oracle values (G(i omega_n) diagonal
+    and E0, written by tests/golden/make_golden.py from the oracle)."""
+    import numpy as np
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "green_tilted12_prefix.json")))
+    w = configs.tilted12_u8()
+    w.mu = w.U / 2
+    ref = np.asarray(gold["G_diag_re"]) + 1j * np.asarray(gold["G_diag_im"])
+    z = 1j * (2 * np.arange(gold["n_matsubara"]) + 1) * np.pi / gold["beta_M"]
+    orb = [(i, 0) for i in range(12)]
+    out = {"workload": f"tilted12 U=8 mu=U/2, MC basis prefix of {gold['n_f']} states, {gold['n_blocks']} blocks, "
+                       f"w_t {gold['w_t']:.6f}, G(i w_n) n<{gold['n_matsubara']} beta_M {gold['beta_M']}"}
+    for key, dt in (("f32", pkg.MCD_F32), ("f64", pkg.MCD_F64)):
+        ctx = pkg.Context(dev.index or 0)
+        ctx.mcd_set_hamiltonian(w.lat.t, w.eps, w.U, w.n_up, w.n_dn)
+        ctx.mcd_build_basis(w.seed, gold["n_f"], w.beta, [w.seed_word()])
+        import torch
+        psi = torch.empty(gold["n_f"], dtype=torch.float32 if dt == pkg.MCD_F32 else torch.float64, device=dev)
+        r = ctx.mcd_lanczos_ground(800, 1e-7 if dt == pkg.MCD_F32 else 1e-13, 0, dt, psi=psi,
+                                   allow_not_converged=True)
+        G, dp, dm = ctx.mcd_band_lanczos_green(orb, gold["n_blocks"], gold["w_t"], z, dtype=dt)
+        d = np.einsum("zaa->za", G)
+        out[key] = {"dE0_vs_oracle": abs(r["E0"] - gold["E0"]),
+                    "max_rel_dG_vs_oracle": float(np.max(np.abs(d - ref)) / np.max(np.abs(ref))),
+                    "dims_match": (dp, dm) == (gold["dim_plus"], gold["dim_minus"])}
+        ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -405,6 +490,9 @@ def main():
                     help="matrix-free H*v kernels (no connection records) on the 4x4 workload")
     ap.add_argument("--no-rect24", action="store_true",
                     help="skip the 6x4 t-t' (24-site, 5e7-state) H*V measurements")
+    ap.add_argument("--no-green", action="store_true", help="skip the band-Lanczos Green-function measurements")
+    ap.add_argument("--green-c5-blocks", type=int, default=40,
+                    help="band blocks per excited space of the 6x4 Green function")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -576,6 +664,11 @@ def main():
 
     if not args.no_rect24:
         out["hv_apply_rect24_fp32"] = rect24_hv(pkg, configs, dev, peak)
+    if not args.no_green:
+        out["green_precision_tilted12_prefix"] = green_precision(pkg, configs, dev)
+        out["band_green_C2"] = band_green(pkg, configs, dev, peak, "tilted12_u8", 1 << 18, 150)
+        out["band_green_C5"] = band_green(pkg, configs, dev, peak, "rect24_u8", 50_000_000, args.green_c5_blocks,
+                                          mu_half=False)
     if not args.no_batch:
         out["impurity_batch"] = impurity_batch(pkg, dev)
 

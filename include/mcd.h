@@ -96,11 +96,12 @@ typedef enum { MCD_F64 = 0, MCD_F32 = 1 } mcd_dtype;
                                    mcd_hv_cache_info).  A reported failure is
                                    cleared, so later calls can succeed. */
 #define MCD_OPT_WAIT_TEST 8      /* test of the time-out path: value k >= 0
-                                   makes the next one-column cached product
-                                   withhold the shared-memory copies of work
-                                   item k of its second pass and poll each
-                                   wait only 4096 times, so that the waits on
-                                   that item give up; -1 = off (default).
+                                   makes the next cached product withhold the
+                                   arrival that completes the shared-memory
+                                   stage of work item k (one column) or work
+                                   unit k (many columns) of its second pass
+                                   and poll each wait only 4096 times, so that
+                                   the waits on it give up; -1 = off (default).
                                    Applies to one product, then resets. */
 #define MCD_OPT_KRYLOV_STORE 9   /* Lanczos vectors of mcd_lanczos_ground:
                                    0 = kept in device memory when they fit in
@@ -110,6 +111,14 @@ typedef enum { MCD_F64 = 0, MCD_F32 = 1 } mcd_dtype;
                                    recursion (same fixed-order reductions, so
                                    the same vectors bit for bit) forms the
                                    Ritz vector. */
+#define MCD_OPT_HV_COLS 10       /* cached H*V with several columns: 0 = the
+                                   first product of each column count (<= 64)
+                                   and dtype of a basis and Hamiltonian times
+                                   both kernels (pipelined column tiles, CTA
+                                   per work item) and later products use the
+                                   faster (default); 1 = pipelined tiles;
+                                   2 = CTA per work item.  Same matrix, summed
+                                   in another order (within rounding). */
 #define MCD_OPT_HASH_ITEM 4     /* states per work item of the hash-lookup
                                    kernels: a power of two in [64, 4096]
                                    (default 1024).  Blocks of more states are
@@ -294,6 +303,33 @@ int mcd_green_gradient(mcd_ctx* ctx, const int* orb_site, const int* orb_spin, i
                        double w_t, const double* z_re, const double* z_im, int nz, const double* gG_re,
                        const double* gG_im, double cg_tol, double* grad_t, double* grad_eps, double* grad_U,
                        int* cg_iters);
+
+/* App. C for many impurity models at once (the embedding use of the
+ * method): for every instance i, mcd_band_lanczos_green on ctxs[i] (its
+ * Hamiltonian, basis and the ground state left by mcd_lanczos_ground or
+ * mcd_batch_lanczos_ground) with the same orbitals, n_block_iter, w_t, dtype
+ * and z points.  G_re, G_im: host [n_inst][nz][L][L]; dim_plus, dim_minus:
+ * host [n_inst] (nullable).  The instances run concurrently: a pool of host
+ * threads, each with its own CUDA stream, takes instances one after another
+ * (every buffer the calls allocate is stream-ordered, so they do not
+ * synchronise the device); each context's stream is restored afterwards and
+ * the results equal those of the one-instance call.  A context appears once.
+ * Returns the first failing instance's status (its message, prefixed with its
+ * index, in ctxs[0]'s last error). */
+int mcd_batch_band_lanczos_green(mcd_ctx* const* ctxs, int n_inst, const int* orb_site, const int* orb_spin,
+                                 int L, int n_block_iter, double w_t, int dtype, const double* z_re,
+                                 const double* z_im, int nz, double* G_re, double* G_im, int64_t* dim_plus,
+                                 int64_t* dim_minus);
+
+/* mcd_green_gradient for many instances at once (gradients with respect to
+ * each instance's bath and cluster parameters), run like
+ * mcd_batch_band_lanczos_green.  Every instance has the same number of sites
+ * n.  gG_re, gG_im: host [n_inst][nz][L][L]; grad_t: host [n_inst][n][n];
+ * grad_eps, grad_U: host [n_inst][n]; cg_iters: host [n_inst] (nullable). */
+int mcd_batch_green_gradient(mcd_ctx* const* ctxs, int n_inst, const int* orb_site, const int* orb_spin, int L,
+                             int n_block_iter, double w_t, const double* z_re, const double* z_im, int nz,
+                             const double* gG_re, const double* gG_im, double cg_tol, double* grad_t,
+                             double* grad_eps, double* grad_U, int* cg_iters);
 
 /* App. B/C (diagonalising the effective matrices): eigenvalues w[n]
  * (ascending) of the symmetric host matrix A[n][n] (row-major; not modified)

@@ -22,7 +22,8 @@ MCD_SAMPLE_NEW_ONLY = 1
 MCD_OPT_HV_ALGO, MCD_OPT_KERNEL_TIMING, MCD_OPT_SAMPLER_THREADS, MCD_OPT_HASH_ITEM = 1, 2, 3, 4
 MCD_OPT_SAMPLER_DEVICE = 5
 MCD_OPT_HV_CACHE = 6
-MCD_OPT_APPLY_SYNC, MCD_OPT_WAIT_TEST, MCD_OPT_KRYLOV_STORE = 7, 8, 9
+MCD_OPT_APPLY_SYNC, MCD_OPT_WAIT_TEST, MCD_OPT_KRYLOV_STORE, MCD_OPT_HV_COLS = 7, 8, 9, 10
+HV_COLS_AUTO, HV_COLS_TILES, HV_COLS_ITEMS = 0, 1, 2
 MCD_E_TIMEOUT = -7
 CACHE_AUTO, CACHE_OFF, CACHE_REQUIRED = 0, 1, 2
 SAMPLER_AUTO, SAMPLER_HOST, SAMPLER_DEVICE = 0, 1, 2
@@ -72,6 +73,14 @@ _SIGS = {
                                           ctypes.c_int, ctypes.c_int, ctypes.c_double, c_dp, c_dp, ctypes.c_int, c_dp,
                                           c_dp, ctypes.c_double, c_dp, c_dp, c_dp, ctypes.POINTER(ctypes.c_int)]),
     "mcd_batch_apply": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, c_vp, c_vp, ctypes.c_int]),
+    "mcd_batch_band_lanczos_green": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                    ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                                    ctypes.c_double, ctypes.c_int, c_dp, c_dp, ctypes.c_int, c_dp,
+                                                    c_dp, c_i64p, c_i64p]),
+    "mcd_batch_green_gradient": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_double, c_dp, c_dp, ctypes.c_int, c_dp, c_dp, ctypes.c_double,
+                                                c_dp, c_dp, c_dp, ctypes.POINTER(ctypes.c_int)]),
     "mcd_batch_lanczos_ground": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                 ctypes.c_uint64, ctypes.c_int, c_dp, ctypes.POINTER(ctypes.c_int),
                                                 c_dp, ctypes.POINTER(c_vp)]),
@@ -161,6 +170,59 @@ def mcd_batch_lanczos_ground(ctxs, max_iter: int, tol: float, seed: int, dtype: 
                                         res.ctypes.data_as(c_dp), parr)
     _batch_check(ctxs, st, "mcd_batch_lanczos_ground", ok=(0, -5) if allow_not_converged else (0,))
     return {"E0": E0, "iters": np.array(list(it)), "residual": res, "status": st}
+
+
+def _orbitals(orbitals):
+    L = len(orbitals)
+    return (L, (ctypes.c_int * L)(*[int(o[0]) for o in orbitals]), (ctypes.c_int * L)(*[int(o[1]) for o in orbitals]))
+
+
+def _zpoints(z):
+    z = np.ascontiguousarray(np.atleast_1d(z), dtype=np.complex128)
+    return z, np.ascontiguousarray(z.real), np.ascontiguousarray(z.imag)
+
+
+def mcd_batch_band_lanczos_green(ctxs, orbitals, n_block_iter: int, w_t: float, z, dtype: int = MCD_F64):
+    """G[n_inst, nz, L, L] (complex) of every context's last ground state, the
+    instances run concurrently; returns (G, dim_plus[n_inst], dim_minus[n_inst])."""
+    for c in ctxs:
+        c._sync_stream()
+    n = len(ctxs)
+    L, site, spin = _orbitals(orbitals)
+    z, zr, zi = _zpoints(z)
+    gr = np.zeros((n, len(z), L, L))
+    gi = np.zeros((n, len(z), L, L))
+    dp = np.zeros(n, dtype=np.int64)
+    dm = np.zeros(n, dtype=np.int64)
+    st = lib().mcd_batch_band_lanczos_green(_ctx_array(ctxs), n, site, spin, L, n_block_iter, w_t, dtype,
+                                            zr.ctypes.data_as(c_dp), zi.ctypes.data_as(c_dp), len(z),
+                                            gr.ctypes.data_as(c_dp), gi.ctypes.data_as(c_dp),
+                                            dp.ctypes.data_as(c_i64p), dm.ctypes.data_as(c_i64p))
+    _batch_check(ctxs, st, "mcd_batch_band_lanczos_green")
+    return gr + 1j * gi, dp, dm
+
+
+def mcd_batch_green_gradient(ctxs, orbitals, n_block_iter: int, w_t: float, z, gG, cg_tol: float = 1e-11,
+                             allow_not_converged: bool = False):
+    """mcd_green_gradient of every context, the instances run concurrently;
+    gG: complex [n_inst, nz, L, L].  Returns (grad_t [n_inst, n, n],
+    grad_eps [n_inst, n], grad_U [n_inst, n], cg_iters [n_inst])."""
+    for c in ctxs:
+        c._sync_stream()
+    n_inst = len(ctxs)
+    L, site, spin = _orbitals(orbitals)
+    z, zr, zi = _zpoints(z)
+    gG = np.asarray(gG, dtype=np.complex128).reshape(n_inst, len(z), L, L)
+    gr, gi = np.ascontiguousarray(gG.real), np.ascontiguousarray(gG.imag)
+    n = ctxs[0].n_sites
+    gt, ge, gu = np.zeros((n_inst, n, n)), np.zeros((n_inst, n)), np.zeros((n_inst, n))
+    it = (ctypes.c_int * n_inst)()
+    st = lib().mcd_batch_green_gradient(_ctx_array(ctxs), n_inst, site, spin, L, n_block_iter, w_t,
+                                        zr.ctypes.data_as(c_dp), zi.ctypes.data_as(c_dp), len(z),
+                                        gr.ctypes.data_as(c_dp), gi.ctypes.data_as(c_dp), cg_tol,
+                                        gt.ctypes.data_as(c_dp), ge.ctypes.data_as(c_dp), gu.ctypes.data_as(c_dp), it)
+    _batch_check(ctxs, st, "mcd_batch_green_gradient", ok=(0, -5) if allow_not_converged else (0,))
+    return gt, ge, gu, np.array(list(it))
 
 
 def _ptr(t) -> int:

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmcd.so")
-SOURCES = ["mcd_api.cu", "index.cu", "hv.cu", "hv_hash.cu", "hv_cache.cu", "hv_cache_cols.cu", "krylov.cu", "band.cu", "adjoint.cu", "noalloc.cu", "sampler.cpp", "sampler_gpu.cu", "batch.cu", "tridiag.cpp",
+SOURCES = ["mcd_api.cu", "index.cu", "hv.cu", "hv_hash.cu", "hv_cache.cu", "hv_cache_cols.cu", "hv_cache_items.cu", "krylov.cu", "band.cu", "adjoint.cu", "noalloc.cu", "sampler.cpp", "sampler_gpu.cu", "batch.cu", "tridiag.cpp",
            "symeig.cpp", "basis_io.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -113,12 +113,92 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ X,
   }
 }
 
+// fp32 vectors: the same partial sums without fp64 multiplies (GB300's fp64
+// rate is a small fraction of its fp32 rate).  Each product is split exactly
+// into p + e (e = fma(x, y, -p)) and summed into a double-float (hi, lo) over
+// one tile of rows; the tile's sum hi + lo is added to the fp64 partial.
+__global__ void __launch_bounds__(kThreads) gram32_kernel(const float* __restrict__ X, int pa,
+                                                          const float* __restrict__ Y, int pb, int ld, int64_t n,
+                                                          double* partials) {
+  constexpr int kRows = 32;
+  __shared__ float xs[kRows][kMaxOrb];
+  __shared__ float ys[kRows][kMaxOrb];
+  const int npair = pa * pb;
+  constexpr int kPer = kMaxOrb * kMaxOrb / kThreads;
+  double acc[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) acc[u] = 0.0;
+  for (int64_t r0 = int64_t(blockIdx.x) * kRows; r0 < n; r0 += int64_t(gridDim.x) * kRows) {
+    for (int e = threadIdx.x; e < kRows * pa; e += kThreads) {
+      const int rr = e / pa, cc = e - rr * pa;
+      const int64_t r = r0 + rr;
+      xs[rr][cc] = r < n ? X[r * ld + cc] : 0.f;
+    }
+    for (int e = threadIdx.x; e < kRows * pb; e += kThreads) {
+      const int rr = e / pb, cc = e - rr * pb;
+      const int64_t r = r0 + rr;
+      ys[rr][cc] = r < n ? Y[r * ld + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int pr = threadIdx.x + u * kThreads;
+      if (pr < npair) {
+        const int ia = pr / pb, ib = pr - (pr / pb) * pb;
+        float hi = 0.f, lo = 0.f;
+        for (int rr = 0; rr < kRows; ++rr) {
+          const float x = xs[rr][ia], y = ys[rr][ib];
+          const float p = x * y;
+          const float e = fmaf(x, y, -p);
+          const float sum = hi + p, bb = sum - hi;
+          lo += ((hi - (sum - bb)) + (p - bb)) + e;
+          hi = sum;
+        }
+        acc[u] += double(hi) + double(lo);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int pr = threadIdx.x + u * kThreads;
+    if (pr < npair) partials[int64_t(blockIdx.x) * npair + pr] = acc[u];
+  }
+}
+
 __global__ void reduce_partials_kernel(const double* partials, int nparts, int npair, double* out) {
   const int pr = blockIdx.x * blockDim.x + threadIdx.x;
   if (pr >= npair) return;
   double s = 0.0;
   for (int i = 0; i < nparts; ++i) s += partials[int64_t(i) * npair + pr];
   out[pr] = s;
+}
+
+// fp32 vectors: the same combination with the fp64 coefficients given as
+// float pairs (hi, lo) (CH / CL, same layout as C1 | C2, beta as bh + bl):
+// each product x c = x ch + x cl is formed exactly as float terms and summed
+// into a double-float (hi, lo), rounded once to float at the end.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x, float ch, float cl) {
+  const float p = x * ch;
+  const float e = fmaf(x, ch, -p) + x * cl;
+  const float sum = hi + p, bb = sum - hi;
+  lo += ((hi - (sum - bb)) + (p - bb)) + e;
+  hi = sum;
+}
+
+__global__ void block_combine32_kernel(const float* W, float* out, int pw, float bh, float bl, const float* X1,
+                                       int p1, const float* CH1, const float* CL1, const float* X2, int p2,
+                                       const float* CH2, const float* CL2, int ld, int64_t n) {
+  const int64_t total = n * pw;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e / pw;
+    const int j = int(e - r * pw);
+    float hi = 0.f, lo = 0.f;
+    if (bh != 0.f || bl != 0.f) df_add(hi, lo, W[r * ld + j], bh, bl);
+    for (int i = 0; i < p1; ++i) df_add(hi, lo, X1[r * ld + i], __ldg(CH1 + i * pw + j), __ldg(CL1 + i * pw + j));
+    for (int i = 0; i < p2; ++i) df_add(hi, lo, X2[r * ld + i], __ldg(CH2 + i * pw + j), __ldg(CL2 + i * pw + j));
+    out[r * ld + j] = hi + lo;
+  }
 }
 
 // W[r][j] = beta * W[r][j] + sum_i X1[r][i] C1[i][j] + sum_i X2[r][i] C2[i][j]
@@ -207,12 +287,109 @@ void factors(int p, int r, const std::vector<int>& piv, const std::vector<double
 }
 
 struct BandRun {
-  std::vector<double> E;   // eigenvalues of H_eff
-  std::vector<double> Q;   // [L][K]
-  std::vector<double> S;   // [K][K] eigenvectors of H_eff (only when the blocks are kept)
+  std::vector<double> E;   // eigenvalues of H_eff (when the blocks are kept)
+  std::vector<double> Q;   // [L][K]                (when the blocks are kept)
+  std::vector<double> S;   // [K][K] eigenvectors of H_eff (when the blocks are kept)
+  // the block tridiagonal H_eff itself: A_k (p_k x p_k), B_{k+1} (p_{k+1} x p_k),
+  // and R0 (p_0 x L) with the start block = V_0 R0
+  std::vector<std::vector<double>> A, B;
+  std::vector<int> ps;
+  std::vector<double> R0;
   int64_t dim = 0;
   int K = 0;
 };
+
+// In-place inverse of the p x p complex matrix M (row-major), Gauss-Jordan
+// with partial pivoting; false when a pivot vanishes.
+bool cinv(int p, std::vector<std::complex<double>>& M) {
+  std::vector<int> perm(p);
+  for (int i = 0; i < p; ++i) perm[i] = i;
+  for (int k = 0; k < p; ++k) {
+    int best = k;
+    double bv = std::abs(M[size_t(k) * p + k]);
+    for (int i = k + 1; i < p; ++i)
+      if (std::abs(M[size_t(i) * p + k]) > bv) { bv = std::abs(M[size_t(i) * p + k]); best = i; }
+    if (!(bv > 0.0)) return false;
+    if (best != k) {
+      for (int j = 0; j < p; ++j) std::swap(M[size_t(k) * p + j], M[size_t(best) * p + j]);
+      std::swap(perm[k], perm[best]);
+    }
+    const std::complex<double> inv = 1.0 / M[size_t(k) * p + k];
+    M[size_t(k) * p + k] = 1.0;
+    for (int j = 0; j < p; ++j) M[size_t(k) * p + j] *= inv;
+    for (int i = 0; i < p; ++i) {
+      if (i == k) continue;
+      const std::complex<double> f = M[size_t(i) * p + k];
+      if (f == 0.0) continue;
+      M[size_t(i) * p + k] = 0.0;
+      for (int j = 0; j < p; ++j) M[size_t(i) * p + j] -= f * M[size_t(k) * p + j];
+    }
+  }
+  // undo the row interchanges as column interchanges of the inverse
+  std::vector<std::complex<double>> out(size_t(p) * p);
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j) out[size_t(i) * p + perm[j]] = M[size_t(i) * p + j];
+  M.swap(out);
+  return true;
+}
+
+// G[z][a][b] += sgn R0[:, a]^T [(w I - H_eff)^{-1}]_{00} R0[:, b] with
+// w = z + E0 (particle run, sgn = +1) or w = -z + E0 (hole run, sgn = -1): the
+// Lehmann sums of App. C over the eigenpairs of H_eff, evaluated without the
+// eigenpairs as the block continued fraction of the block tridiagonal H_eff
+// (Schur complements from the last block up: S_k = w - A_k - B_{k+1}^T
+// S_{k+1}^{-1} B_{k+1}, then S_0^{-1} is the (0, 0) block of the resolvent).
+bool band_resolvent(const BandRun& R, int L, double E0, bool particle, const double* z_re, const double* z_im,
+                    int nz, double* G_re, double* G_im) {
+  using cd = std::complex<double>;
+  const int nb = int(R.A.size());
+  if (nb == 0) return true;
+  const int p0 = R.ps[0];
+  std::vector<cd> S, T, Sn;
+  for (int iz = 0; iz < nz; ++iz) {
+    const cd z(z_re[iz], z_im[iz]);
+    const cd w = particle ? z + E0 : -z + E0;
+    const double sgn = particle ? 1.0 : -1.0;
+    int p = R.ps[nb - 1];
+    S.assign(size_t(p) * p, 0.0);
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < p; ++j) S[size_t(i) * p + j] = (i == j ? w : cd(0.0)) - R.A[nb - 1][size_t(i) * p + j];
+    for (int k = nb - 2; k >= 0; --k) {
+      if (!cinv(p, S)) return false;             // S_{k+1}^{-1}
+      const int q = R.ps[k];                      // B_{k+1}: p x q
+      const std::vector<double>& B = R.B[k];
+      T.assign(size_t(p) * q, 0.0);               // S^{-1} B
+      for (int i = 0; i < p; ++i)
+        for (int l = 0; l < p; ++l) {
+          const cd sv = S[size_t(i) * p + l];
+          if (sv == 0.0) continue;
+          for (int j = 0; j < q; ++j) T[size_t(i) * q + j] += sv * B[size_t(l) * q + j];
+        }
+      Sn.assign(size_t(q) * q, 0.0);
+      for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) {
+          cd acc = (i == j ? w : cd(0.0)) - R.A[k][size_t(i) * q + j];
+          for (int l = 0; l < p; ++l) acc -= B[size_t(l) * q + i] * T[size_t(l) * q + j];
+          Sn[size_t(i) * q + j] = acc;
+        }
+      S.swap(Sn);
+      p = q;
+    }
+    if (!cinv(p0, S)) return false;
+    for (int a = 0; a < L; ++a)
+      for (int b = 0; b < L; ++b) {
+        cd acc = 0.0;
+        for (int i = 0; i < p0; ++i) {
+          const double ra = R.R0[size_t(i) * L + a];
+          if (ra == 0.0) continue;
+          for (int j = 0; j < p0; ++j) acc += ra * S[size_t(i) * p0 + j] * R.R0[size_t(j) * L + b];
+        }
+        G_re[(size_t(iz) * L + a) * L + b] += sgn * acc.real();
+        G_im[(size_t(iz) * L + a) * L + b] += sgn * acc.imag();
+      }
+  }
+  return true;
+}
 
 // dst[r][off + j] = src[r][j] (j < p): one Krylov block into the kept [n][kmax] array
 template <typename T>
@@ -232,16 +409,20 @@ class BandLanczos {
   ~BandLanczos() {
     for (void* p : {static_cast<void*>(B_[0]), static_cast<void*>(B_[1]), static_cast<void*>(B_[2]),
                     static_cast<void*>(part_), static_cast<void*>(gram_), static_cast<void*>(coef_)})
-      if (p) cudaFree(p);
+      if (p) cudaFreeAsync(p, c_->stream);
   }
 
   int alloc() {
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&B_[i], size_t(n_) * L_ * sizeof(T) + 64);
+    cudaStream_t s = c_->stream;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+      e = cudaMallocAsync(reinterpret_cast<void**>(&B_[i]), size_t(n_) * L_ * sizeof(T) + 64, s);
     nparts_ = grid_for(n_ / 32 + 1);
-    if (e == cudaSuccess) e = cudaMalloc(&part_, sizeof(double) * size_t(nparts_) * kMaxOrb * kMaxOrb);
-    if (e == cudaSuccess) e = cudaMalloc(&gram_, sizeof(double) * kMaxOrb * kMaxOrb);
-    if (e == cudaSuccess) e = cudaMalloc(&coef_, sizeof(double) * 2 * kMaxOrb * kMaxOrb);
+    if (e == cudaSuccess)
+      e = cudaMallocAsync(reinterpret_cast<void**>(&part_), sizeof(double) * size_t(nparts_) * kMaxOrb * kMaxOrb, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&gram_), sizeof(double) * kMaxOrb * kMaxOrb, s);
+    if (e == cudaSuccess)
+      e = cudaMallocAsync(reinterpret_cast<void**>(&coef_), sizeof(double) * 2 * kMaxOrb * kMaxOrb, s);
     if (e != cudaSuccess) return cuda_fail(c_, e, "band Lanczos buffers");
     return MCD_OK;
   }
@@ -255,7 +436,10 @@ class BandLanczos {
   // host G = X[:, :pa]^T Y[:, :pb]
   int gram(const T* X, int pa, const T* Y, int pb, std::vector<double>& G) {
     cudaStream_t s = c_->stream;
-    gram_kernel<T><<<nparts_, kThreads, 0, s>>>(X, pa, Y, pb, L_, n_, part_);
+    if constexpr (sizeof(T) == 4)
+      gram32_kernel<<<nparts_, kThreads, 0, s>>>(X, pa, Y, pb, L_, n_, part_);
+    else
+      gram_kernel<T><<<nparts_, kThreads, 0, s>>>(X, pa, Y, pb, L_, n_, part_);
     MCD_LAUNCHED(c_);
     reduce_partials_kernel<<<(pa * pb + 255) / 256, 256, 0, s>>>(part_, nparts_, pa * pb, gram_);
     MCD_LAUNCHED(c_);
@@ -272,10 +456,29 @@ class BandLanczos {
     std::vector<double> buf(2 * size_t(kMaxOrb) * kMaxOrb, 0.0);
     std::copy(C1.begin(), C1.begin() + size_t(p1) * pw, buf.begin());
     if (p2) std::copy(C2.begin(), C2.begin() + size_t(p2) * pw, buf.begin() + size_t(kMaxOrb) * kMaxOrb);
-    cudaError_t e = cudaMemcpyAsync(coef_, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
-    block_combine_kernel<T><<<grid_for(n_ * pw), kThreads, 0, s>>>(W, out, pw, beta, X1, p1, coef_, X2 ? X2 : X1,
-                                                                   p2, coef_ + size_t(kMaxOrb) * kMaxOrb, L_, n_);
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+      // float pairs (hi, lo) of every coefficient: [hi C1 | hi C2 | lo C1 | lo C2]
+      const size_t m = size_t(kMaxOrb) * kMaxOrb;
+      std::vector<float> f(4 * m);
+      for (size_t i = 0; i < 2 * m; ++i) {
+        const float h = float(buf[i]);
+        f[i] = h;
+        f[2 * m + i] = float(buf[i] - double(h));
+      }
+      e = cudaMemcpyAsync(coef_, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
+      const float* ch = reinterpret_cast<const float*>(coef_);
+      const float* cl = ch + 2 * m;
+      const float bh = float(beta), bl = float(beta - double(bh));
+      block_combine32_kernel<<<grid_for(n_ * pw), kThreads, 0, s>>>(W, out, pw, bh, bl, X1, p1, ch, cl,
+                                                                     X2 ? X2 : X1, p2, ch + m, cl + m, L_, n_);
+    } else {
+      e = cudaMemcpyAsync(coef_, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
+      block_combine_kernel<T><<<grid_for(n_ * pw), kThreads, 0, s>>>(W, out, pw, beta, X1, p1, coef_, X2 ? X2 : X1,
+                                                                     p2, coef_ + size_t(kMaxOrb) * kMaxOrb, L_, n_);
+    }
     MCD_LAUNCHED(c_);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // coef_ is reused by the next call
@@ -400,8 +603,20 @@ class BandLanczos {
       p = r;
       std::swap(Vprev, Vcur);   // Vcur <- new block, Vprev <- old current
     }
-    // assemble the block tridiagonal H_eff
     const int nb = int(As.size());
+    out.ps.assign(ps.begin(), ps.begin() + nb);
+    out.A = As;
+    out.B.assign(Bs.begin(), Bs.begin() + std::max(nb - 1, 0));
+    out.R0 = R0;
+    out.dim = n_;
+    if (!vall_) {
+      // G from the band matrix itself (band_resolvent): no eigenpairs needed
+      int K = 0;
+      for (int k = 0; k < nb; ++k) K += ps[k];
+      out.K = K;
+      return MCD_OK;
+    }
+    // assemble the block tridiagonal H_eff
     std::vector<int> off(nb + 1, 0);
     for (int k = 0; k < nb; ++k) off[k + 1] = off[k] + ps[k];
     const int K = off[nb];
@@ -597,13 +812,13 @@ int grad_side(mcd_ctx* c, mcd_ctx* sub, const double* vall, int64_t N, const Ban
     }
   cudaStream_t s = c->stream;
   double *dM = nullptr, *U = nullptr, *V2 = nullptr, *F = nullptr;
-  cudaError_t e = cudaMalloc(&dM, sizeof(double) * (size_t(K) * K * 2 + size_t(K) * L));
-  if (e == cudaSuccess) e = cudaMalloc(&U, sizeof(double) * size_t(N) * K);
-  if (e == cudaSuccess) e = cudaMalloc(&V2, sizeof(double) * size_t(N) * K);
-  if (e == cudaSuccess) e = cudaMalloc(&F, sizeof(double) * size_t(N) * L);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dM), sizeof(double) * (size_t(K) * K * 2 + size_t(K) * L), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&U), sizeof(double) * size_t(N) * K, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&V2), sizeof(double) * size_t(N) * K, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&F), sizeof(double) * size_t(N) * L, s);
   auto release = [&]() {
     for (double* q : {dM, U, V2, F})
-      if (q) cudaFree(q);
+      if (q) cudaFreeAsync(q, s);
   };
   if (e != cudaSuccess) {
     release();
@@ -646,62 +861,368 @@ int grad_side(mcd_ctx* c, mcd_ctx* sub, const double* vall, int64_t N, const Ban
   return e == cudaSuccess ? MCD_OK : cuda_fail(c, e, "Green gradient: start-vector term");
 }
 
+// ---- target-weight truncation and excited bases on the device -----------------
+
+// Sec. "Further truncation": with w_i = (psi_i / |psi|)^2 sorted descending
+// (ties: lower index first), keep the shortest prefix whose weight reaches
+// w_t of the total.  Without sorting: tau = the weight at the cut is the
+// largest value with sum_{w_i >= tau} w_i >= target, found by bisection over
+// the bit patterns of non-negative doubles (ordered like the values); every
+// weight above tau is kept and, of those equal to tau, the m of lowest index
+// that the target needs.  Every sum is a fixed-order reduction (kTrParts
+// block partials summed by one thread), so the cut repeats bit for bit.
+constexpr int kTrParts = 1024;
+constexpr int kTrThreads = 256;
+
+struct TrState {
+  double inv;        // 1 / |psi|
+  double total;      // sum of the weights
+  double target;     // w_t * total (1 - 1e-15)
+  uint64_t lo, hi;   // bisection bounds (bit patterns): S(lo) >= target > S(hi)
+  double s_gt;       // sum of the weights above tau
+  uint32_t n_eq;     // weights equal to tau
+  uint32_t m;        // of those, kept (lowest indices)
+};
+
+// mode 0: psi^2; 1: w; 2: w where bits(w) >= (lo + hi) / 2; 3: w > tau (sum)
+// and w == tau (count), tau = lo
+template <int MODE>
+__global__ void __launch_bounds__(kTrThreads) trunc_sum_kernel(const double* __restrict__ psi, int64_t n,
+                                                              const TrState* st, double* part, uint32_t* cpart) {
+  __shared__ double sd[kTrThreads];
+  __shared__ uint32_t sc[kTrThreads];
+  const double inv = MODE == 0 ? 1.0 : st->inv;
+  uint64_t thr = 0;
+  if (MODE == 2) thr = st->lo + (st->hi - st->lo) / 2;
+  if (MODE == 3) thr = st->lo;
+  double acc = 0.0;
+  uint32_t cnt = 0;
+  for (int64_t i = int64_t(blockIdx.x) * kTrThreads + threadIdx.x; i < n; i += int64_t(kTrParts) * kTrThreads) {
+    const double p = psi[i] * inv;
+    const double w = p * p;
+    const uint64_t b = uint64_t(__double_as_longlong(w));
+    if (MODE <= 1) acc += w;
+    if (MODE == 2 && b >= thr) acc += w;
+    if (MODE == 3) {
+      if (b > thr) acc += w;
+      if (b == thr) ++cnt;
+    }
+  }
+  sd[threadIdx.x] = acc;
+  sc[threadIdx.x] = cnt;
+  __syncthreads();
+  for (int o = kTrThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sd[threadIdx.x] += sd[threadIdx.x + o];
+      sc[threadIdx.x] += sc[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sd[0];
+    cpart[blockIdx.x] = sc[0];
+  }
+}
+
+// one thread: the partials in order, then the state update of the mode
+template <int MODE>
+__global__ void trunc_step_kernel(const double* part, const uint32_t* cpart, TrState* st, double w_t) {
+  double s = 0.0;
+  uint64_t c = 0;
+  for (int b = 0; b < kTrParts; ++b) {
+    s += part[b];
+    c += cpart[b];
+  }
+  if (MODE == 0) {
+    st->inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  } else if (MODE == 1) {
+    st->total = s;
+    st->target = w_t * s * (1.0 - 1e-15);
+    st->lo = 0;
+    st->hi = 0x7FF0000000000000ull;   // +inf: no weight reaches it
+  } else if (MODE == 2) {
+    const uint64_t mid = st->lo + (st->hi - st->lo) / 2;
+    if (st->hi - st->lo > 1) {
+      if (s >= st->target) st->lo = mid;
+      else st->hi = mid;
+    }
+  } else {
+    const double tau = __longlong_as_double(static_cast<long long>(st->lo));
+    st->s_gt = s;
+    st->n_eq = uint32_t(c);
+    // smallest m with s_gt + m tau >= target (at least one: tau's own state)
+    uint64_t m = 1;
+    if (tau > 0.0) {
+      const double need = (st->target - s) / tau;
+      m = need > 1.0 ? uint64_t(ceil(need)) : 1;
+      while (m > 1 && s + double(m - 1) * tau >= st->target) --m;
+      while (m < c && s + double(m) * tau < st->target) ++m;
+    } else {
+      m = c;
+    }
+    st->m = uint32_t(m < c ? m : c);
+  }
+}
+
+// eq[i] = (w_i == tau)
+__global__ void trunc_eq_kernel(const double* __restrict__ psi, int64_t n, const TrState* st, uint32_t* eq) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double p = psi[i] * st->inv;
+  eq[i] = uint64_t(__double_as_longlong(p * p)) == st->lo ? 1u : 0u;
+}
+
+// keep[i] = w_i > tau, or w_i == tau among the first m such (eqpos = exclusive scan of eq)
+__global__ void trunc_keep_kernel(const double* __restrict__ psi, int64_t n, const TrState* st,
+                                  const uint32_t* eqpos, uint32_t* keep) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double p = psi[i] * st->inv;
+  const uint64_t b = uint64_t(__double_as_longlong(p * p));
+  keep[i] = (b > st->lo || (b == st->lo && eqpos[i] < st->m)) ? 1u : 0u;
+}
+
+// the kept states in index order: basis index, word, psi value
+__global__ void trunc_compact_kernel(const double* __restrict__ psi, const uint64_t* __restrict__ words, int64_t n,
+                                     const uint32_t* keep, const uint32_t* pos, uint32_t* idx, uint64_t* kw,
+                                     double* kc) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n || !keep[i]) return;
+  const uint32_t p = pos[i];
+  idx[p] = uint32_t(i);
+  kw[p] = words[i];
+  kc[p] = psi[i];
+}
+
+__global__ void __launch_bounds__(kTrThreads) sq_part_kernel(const double* __restrict__ v, int64_t n, double* part) {
+  __shared__ double sd[kTrThreads];
+  double acc = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * kTrThreads + threadIdx.x; i < n; i += int64_t(kTrParts) * kTrThreads)
+    acc += v[i] * v[i];
+  sd[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kTrThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sd[threadIdx.x] += sd[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sd[0];
+}
+
+__global__ void scale_vec_kernel(double* v, int64_t n, const double* part) {
+  __shared__ double f;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < kTrParts; ++b) s += part[b];
+    f = 1.0 / sqrt(s);
+  }
+  __syncthreads();
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    v[i] *= f;
+}
+
+// Kept ground state on the device: idx (ascending basis indices), words and
+// renormalised coefficients of the kept states; kn = |P psi|^2 / |psi|^2.
+struct KeptDev {
+  uint32_t* idx = nullptr;
+  uint64_t* words = nullptr;
+  double* coef = nullptr;
+  int64_t n = 0;
+  double kn = 0.0;
+  cudaStream_t s = nullptr;
+  ~KeptDev() {
+    for (void* p : {static_cast<void*>(idx), static_cast<void*>(words), static_cast<void*>(coef)})
+      if (p) cudaFreeAsync(p, s);
+  }
+};
+
+int kept_ground_state_dev(mcd_ctx* c, double w_t, KeptDev& out) {
+  const int64_t N = c->idx.n;
+  cudaStream_t s = c->stream;
+  out.s = s;
+  const double* psi = c->gs_psi;
+  // work: TrState | partials | counts | eq/eqpos | keep | pos
+  const size_t off_part = 64, off_cnt = off_part + sizeof(double) * kTrParts,
+               off_eq = off_cnt + sizeof(uint32_t) * kTrParts + 64;
+  const size_t off_keep = off_eq + sizeof(uint32_t) * size_t(N) + 64, off_pos = off_keep + sizeof(uint32_t) * size_t(N) + 64;
+  unsigned char* wk = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&wk), off_pos + sizeof(uint32_t) * size_t(N) + 64, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "truncation work");
+  struct Free {
+    void* p;
+    cudaStream_t s;
+    ~Free() { cudaFreeAsync(p, s); }
+  } guard{wk, s};
+  TrState* st = reinterpret_cast<TrState*>(wk);
+  double* part = reinterpret_cast<double*>(wk + off_part);
+  uint32_t* cpart = reinterpret_cast<uint32_t*>(wk + off_cnt);
+  uint32_t* eq = reinterpret_cast<uint32_t*>(wk + off_eq);
+  uint32_t* keep = reinterpret_cast<uint32_t*>(wk + off_keep);
+  uint32_t* pos = reinterpret_cast<uint32_t*>(wk + off_pos);
+  trunc_sum_kernel<0><<<kTrParts, kTrThreads, 0, s>>>(psi, N, st, part, cpart);
+  trunc_step_kernel<0><<<1, 1, 0, s>>>(part, cpart, st, w_t);
+  trunc_sum_kernel<1><<<kTrParts, kTrThreads, 0, s>>>(psi, N, st, part, cpart);
+  trunc_step_kernel<1><<<1, 1, 0, s>>>(part, cpart, st, w_t);
+  c->launches += 4;
+  for (int it = 0; it < 64; ++it) {
+    trunc_sum_kernel<2><<<kTrParts, kTrThreads, 0, s>>>(psi, N, st, part, cpart);
+    trunc_step_kernel<2><<<1, 1, 0, s>>>(part, cpart, st, w_t);
+    c->launches += 2;
+  }
+  trunc_sum_kernel<3><<<kTrParts, kTrThreads, 0, s>>>(psi, N, st, part, cpart);
+  trunc_step_kernel<3><<<1, 1, 0, s>>>(part, cpart, st, w_t);
+  const int g = int((N + 255) / 256);
+  trunc_eq_kernel<<<g, 256, 0, s>>>(psi, N, st, eq);
+  c->launches += 3;
+  e = scan_u32(c, eq, eq, N, s);
+  if (e == cudaSuccess) {
+    trunc_keep_kernel<<<g, 256, 0, s>>>(psi, N, st, eq, keep);
+    MCD_LAUNCHED(c);
+    e = scan_u32(c, keep, pos, N, s);
+  }
+  uint32_t last_pos = 0, last_keep = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&last_pos, pos + N - 1, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&last_keep, keep + N - 1, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "truncation");
+  const int64_t nk = int64_t(last_pos) + last_keep;
+  if (nk < 1) return fail(c, MCD_E_BREAKDOWN, "truncation kept no state (zero ground state)");
+  e = cudaMallocAsync(reinterpret_cast<void**>(&out.idx), sizeof(uint32_t) * size_t(nk), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&out.words), sizeof(uint64_t) * size_t(nk), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&out.coef), sizeof(double) * size_t(nk), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "kept ground state");
+  out.n = nk;
+  trunc_compact_kernel<<<g, 256, 0, s>>>(psi, c->idx.words, N, keep, pos, out.idx, out.words, out.coef);
+  // |P psi|^2 (psi as stored), then the kept coefficients renormalised
+  sq_part_kernel<<<kTrParts, kTrThreads, 0, s>>>(out.coef, nk, part);
+  c->launches += 2;
+  double kn_raw = 0.0, inv = 0.0;
+  std::vector<double> hp(kTrParts);
+  e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * kTrParts, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&inv, &st->inv, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) {
+    scale_vec_kernel<<<int(std::min<int64_t>((nk + 255) / 256, 4096)), 256, 0, s>>>(out.coef, nk, part);
+    MCD_LAUNCHED(c);
+    e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "kept ground state");
+  for (double v : hp) kn_raw += v;
+  out.kn = kn_raw * inv * inv;
+  return MCD_OK;
+}
+
+// The excited basis (Sec. "Subspace of the Green function") on the device:
+// the distinct words c^dag_mu w (dagger) or c_mu w over the kept words w and
+// the orbitals (all of one spin) in orbmask, ascending.
+__global__ void exc_count_kernel(const uint64_t* __restrict__ gw, int64_t ng, uint64_t orbmask, int dagger,
+                                 uint32_t* cnt) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= ng) return;
+  const uint64_t w = gw[i];
+  cnt[i] = uint32_t(__popcll(dagger ? (~w & orbmask) : (w & orbmask)));
+}
+
+__global__ void exc_write_kernel(const uint64_t* __restrict__ gw, int64_t ng, uint64_t orbmask, int dagger,
+                                 const uint32_t* pos, uint64_t* out) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= ng) return;
+  const uint64_t w = gw[i];
+  uint64_t m = dagger ? (~w & orbmask) : (w & orbmask);
+  uint32_t p = pos[i];
+  while (m) {
+    const uint64_t b = m & (~m + 1);
+    out[p++] = w ^ b;
+    m ^= b;
+  }
+}
+
+int excited_basis_dev(mcd_ctx* c, const uint64_t* gw, int64_t ng, uint64_t orbmask, bool dagger, uint64_t** exc,
+                      int64_t* nexc) {
+  *exc = nullptr;
+  *nexc = 0;
+  cudaStream_t s = c->stream;
+  uint32_t* cnt = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * size_t(ng) + 16, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "excited basis counts");
+  const int g = int((ng + 255) / 256);
+  exc_count_kernel<<<g, 256, 0, s>>>(gw, ng, orbmask, dagger ? 1 : 0, cnt);
+  MCD_LAUNCHED(c);
+  uint32_t last_cnt = 0, last_pos = 0;
+  e = cudaMemcpyAsync(&last_cnt, cnt + ng - 1, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = scan_u32(c, cnt, cnt, ng, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&last_pos, cnt + ng - 1, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  const int64_t total = int64_t(last_pos) + last_cnt;
+  uint64_t* cand = nullptr;
+  if (e == cudaSuccess && total > 0) e = cudaMallocAsync(reinterpret_cast<void**>(&cand), sizeof(uint64_t) * size_t(total), s);
+  if (e == cudaSuccess && total > 0) {
+    exc_write_kernel<<<g, 256, 0, s>>>(gw, ng, orbmask, dagger ? 1 : 0, cnt, cand);
+    MCD_LAUNCHED(c);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(cnt, s);
+  if (e != cudaSuccess) {
+    if (cand) cudaFreeAsync(cand, s);
+    return cuda_fail(c, e, "excited basis candidates");
+  }
+  if (total == 0) return MCD_OK;
+  const int st = sort_unique_device(c, cand, total, 2 * c->n, exc, nexc);
+  cudaFreeAsync(cand, s);
+  return st;
+}
+
 template <typename T>
-int one_side(mcd_ctx* c, const std::vector<uint64_t>& kept_w, const std::vector<double>& kept_c, const int* site,
-             const int* spin, int L, bool dagger, int n_blocks, BandRun& out, GradSide* gs = nullptr) {
+int one_side(mcd_ctx* c, const uint64_t* dgw, const double* dgc, int64_t ng, const int* site, const int* spin,
+             int L, bool dagger, int n_blocks, BandRun& out, GradSide* gs = nullptr) {
   const int n = c->n;
   const int sp = spin[0];
-  // excited basis (host): c^dag_mu w or c_mu w over kept w
-  std::vector<uint64_t> exc;
-  exc.reserve(kept_w.size() * L);
-  for (uint64_t w : kept_w)
-    for (int mu = 0; mu < L; ++mu) {
-      const uint64_t bit = 1ull << (spin[mu] == 0 ? n + site[mu] : site[mu]);
-      const bool occ = (w & bit) != 0;
-      if (dagger && !occ) exc.push_back(w | bit);
-      if (!dagger && occ) exc.push_back(w ^ bit);
+  cudaStream_t s = c->stream;
+  // excited basis: c^dag_mu w or c_mu w over the kept w, on the device
+  uint64_t orbmask = 0;
+  for (int mu = 0; mu < L; ++mu) orbmask |= 1ull << (spin[mu] == 0 ? n + site[mu] : site[mu]);
+  uint64_t* exc = nullptr;
+  int64_t nexc = 0;
+  int st = excited_basis_dev(c, dgw, ng, orbmask, dagger, &exc, &nexc);
+  if (st != MCD_OK) return st;
+  struct FreeExc {
+    uint64_t*& p;
+    cudaStream_t s;
+    ~FreeExc() {
+      if (p) cudaFreeAsync(p, s);
     }
-  std::sort(exc.begin(), exc.end());
-  exc.erase(std::unique(exc.begin(), exc.end()), exc.end());
-  out.dim = int64_t(exc.size());
-  if (exc.empty()) {
+  } free_exc{exc, s};
+  out.dim = nexc;
+  if (nexc == 0) {
     out.K = 0;
     return MCD_OK;
   }
   const int dnu = dagger ? 1 : -1;
   const int nup = c->n_up + (sp == 0 ? dnu : 0), ndn = c->n_dn + (sp == 1 ? dnu : 0);
   mcd_ctx* sub = nullptr;
-  int st = mcd_create(&sub, c->device, c->stream);
+  st = mcd_create(&sub, c->device, c->stream);
   if (st) return fail(c, st, "band Lanczos: internal context");
   struct Guard {
     mcd_ctx* p;
     ~Guard() { mcd_destroy(p); }
   } guard{sub};
   sub->hv_algo = c->hv_algo;
+  sub->hv_cache = c->hv_cache;
+  sub->timing = c->timing;   // its products count in this context's kernel times
+  sub->tm = c->tm;
+  sub->tm_borrowed = true;
   st = mcd_set_hamiltonian(sub, n, c->t.data(), c->eps.data(), c->U.data(), n, nup, ndn);
-  if (st == MCD_OK) st = mcd_set_basis(sub, exc.data(), int64_t(exc.size()));
+  if (st == MCD_OK) st = mcd_set_basis_device(sub, exc, nexc);
   if (st != MCD_OK) return fail(c, st, std::string("band Lanczos: excited space: ") + sub->err);
+  cudaFreeAsync(exc, s);
+  exc = nullptr;
   c->launches += sub->launches;
   const int64_t before = sub->launches;
-  // kept ground-state words and coefficients on the device
-  uint64_t* dgw = nullptr;
-  double* dgc = nullptr;
-  cudaStream_t s = c->stream;
-  cudaError_t e = cudaMalloc(&dgw, kept_w.size() * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&dgc, kept_c.size() * 8);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dgw, kept_w.data(), kept_w.size() * 8, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dgc, kept_c.data(), kept_c.size() * 8, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) {
-    cudaFree(dgw);
-    cudaFree(dgc);
-    return cuda_fail(c, e, "ground-state words");
-  }
+  cudaError_t e = cudaSuccess;
   BandLanczos<T> bl(sub, L);
   st = bl.alloc();
   double* vall = nullptr;
   const int kmax = n_blocks * L;
   if (st == MCD_OK && gs) {
-    if (cudaMalloc(&vall, sizeof(double) * size_t(exc.size()) * kmax) != cudaSuccess) {
+    if (cudaMallocAsync(reinterpret_cast<void**>(&vall), sizeof(double) * size_t(nexc) * kmax, s) != cudaSuccess) {
       vall = nullptr;
       st = fail(c, MCD_E_OOM, "Green gradient: the Krylov blocks of an excited space do not fit");
     } else {
@@ -718,9 +1239,8 @@ int one_side(mcd_ctx* c, const std::vector<uint64_t>& kept_w, const std::vector<
       op.site[mu] = site[mu];
       op.spin[mu] = spin[mu];
     }
-    const int64_t ne = int64_t(exc.size());
-    start_vec_kernel<T><<<int((ne + 255) / 256), 256, 0, s>>>(sub->idx.words, ne, dgw, dgc,
-                                                              int64_t(kept_w.size()), bl.buf(0), L, op);
+    const int64_t ne = nexc;
+    start_vec_kernel<T><<<int((ne + 255) / 256), 256, 0, s>>>(sub->idx.words, ne, dgw, dgc, ng, bl.buf(0), L, op);
     MCD_LAUNCHED(sub);
     e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_fail(c, e, "start vectors");
@@ -733,12 +1253,10 @@ int one_side(mcd_ctx* c, const std::vector<uint64_t>& kept_w, const std::vector<
   c->launches += sub->launches - before;
   if (st == MCD_OK && gs) {
     const int64_t b2 = sub->launches;
-    st = grad_side(c, sub, vall, int64_t(exc.size()), out, L, dagger, dgw, int64_t(kept_w.size()), op, *gs);
+    st = grad_side(c, sub, vall, nexc, out, L, dagger, dgw, ng, op, *gs);
     c->launches += sub->launches - b2;
   }
-  if (vall) cudaFree(vall);
-  cudaFree(dgw);
-  cudaFree(dgc);
+  if (vall) cudaFreeAsync(vall, s);
   return st;
 }
 
@@ -757,54 +1275,29 @@ int check_orbitals(mcd_ctx* c, const int* site, const int* spin, int L, int n_bl
   return MCD_OK;
 }
 
-// Target-weight truncation (Sec. "Further truncation"): largest |c|^2 first,
-// ties by basis index, shortest prefix reaching w_t of the norm.  psi = the
-// normalised ground state (host), keep = kept basis indices (ascending), kw/kc
-// = their words and renormalised coefficients, kn = |P psi|^2.
-int kept_ground_state(mcd_ctx* c, double w_t, std::vector<double>& psi, std::vector<int64_t>& keep,
-                      std::vector<uint64_t>& kw, std::vector<double>& kc, double& kn) {
-  const int64_t N = c->idx.n;
+// The device truncation's result on the host (the Green gradient works on
+// the kept words there): psi = the normalised ground state, keep = the kept
+// basis indices (ascending), kw / kc = their words and renormalised
+// coefficients.
+int kept_to_host(mcd_ctx* c, const KeptDev& kd, std::vector<double>& psi, std::vector<int64_t>& keep,
+                 std::vector<uint64_t>& kw, std::vector<double>& kc) {
+  const int64_t N = c->idx.n, nk = kd.n;
+  cudaStream_t s = c->stream;
   psi.resize(N);
-  cudaError_t e = cudaMemcpyAsync(psi.data(), c->gs_psi, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "copy ground state");
+  std::vector<uint32_t> idx(nk);
+  kw.resize(nk);
+  kc.resize(nk);
+  cudaError_t e = cudaMemcpyAsync(psi.data(), c->gs_psi, sizeof(double) * N, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(idx.data(), kd.idx, sizeof(uint32_t) * nk, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(kw.data(), kd.words, sizeof(uint64_t) * nk, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(kc.data(), kd.coef, sizeof(double) * nk, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "kept ground state to host");
+  keep.assign(idx.begin(), idx.end());
   double nn = 0.0;
   for (double v : psi) nn += v * v;
   const double inv = 1.0 / std::sqrt(nn);
-  std::vector<double> wgt(N);
-  for (int64_t i = 0; i < N; ++i) {
-    const double p = psi[i] * inv;
-    wgt[i] = p * p;
-  }
-  std::vector<int64_t> order(N);
-  for (int64_t i = 0; i < N; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return wgt[a] > wgt[b]; });
-  std::vector<double> cum(N);
-  double run = 0.0;
-  for (int64_t i = 0; i < N; ++i) cum[i] = (run += wgt[order[i]]);
-  const double target = w_t * cum[N - 1] * (1.0 - 1e-15);
-  int64_t k = int64_t(std::lower_bound(cum.begin(), cum.end(), target) - cum.begin()) + 1;
-  if (k > N) k = N;
-  keep.assign(order.begin(), order.begin() + k);
-  std::sort(keep.begin(), keep.end());
-  kw.resize(k);
-  kc.resize(k);
-  kn = 0.0;
-  for (int64_t i = 0; i < k; ++i) {
-    kw[i] = c->basis_on_host ? c->basis[keep[i]] : 0;
-    kc[i] = psi[keep[i]];
-    kn += kc[i] * kc[i];
-  }
-  if (!c->basis_on_host) {
-    std::vector<uint64_t> all(N);
-    e = cudaMemcpy(all.data(), c->idx.words, sizeof(uint64_t) * N, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(c, e, "copy basis");
-    for (int64_t i = 0; i < k; ++i) kw[i] = all[keep[i]];
-  }
-  for (double& v : kc) v /= std::sqrt(kn);
-  // psi and kn for a normalised psi
   for (double& v : psi) v *= inv;
-  kn *= inv * inv;
   return MCD_OK;
 }
 
@@ -815,43 +1308,26 @@ int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int 
                        int64_t* dim_plus, int64_t* dim_minus) {
   int st0 = check_orbitals(c, site, spin, L, n_blocks, w_t);
   if (st0 != MCD_OK) return st0;
-  std::vector<double> psi, kc;
-  std::vector<int64_t> keep;
-  std::vector<uint64_t> kw;
-  double kn = 0.0;
-  st0 = kept_ground_state(c, w_t, psi, keep, kw, kc, kn);
+  KeptDev kd;
+  st0 = kept_ground_state_dev(c, w_t, kd);
   if (st0 != MCD_OK) return st0;
   BandRun plus, minus;
-  int st = dtype == MCD_F64 ? one_side<double>(c, kw, kc, site, spin, L, true, n_blocks, plus)
-                            : one_side<float>(c, kw, kc, site, spin, L, true, n_blocks, plus);
+  int st = dtype == MCD_F64 ? one_side<double>(c, kd.words, kd.coef, kd.n, site, spin, L, true, n_blocks, plus)
+                            : one_side<float>(c, kd.words, kd.coef, kd.n, site, spin, L, true, n_blocks, plus);
   if (st == MCD_OK)
-    st = dtype == MCD_F64 ? one_side<double>(c, kw, kc, site, spin, L, false, n_blocks, minus)
-                          : one_side<float>(c, kw, kc, site, spin, L, false, n_blocks, minus);
+    st = dtype == MCD_F64 ? one_side<double>(c, kd.words, kd.coef, kd.n, site, spin, L, false, n_blocks, minus)
+                          : one_side<float>(c, kd.words, kd.coef, kd.n, site, spin, L, false, n_blocks, minus);
   if (st != MCD_OK) return st;
   if (dim_plus) *dim_plus = plus.dim;
   if (dim_minus) *dim_minus = minus.dim;
-  // Lehmann sums: G+ = sum Q Q / (z + E0 - E+), G- = sum Q Q / (z - E0 + E-)
+  // G+ = R0+^T (z + E0 - H+_eff)^{-1} R0+ and G- = R0-^T (z - E0 + H-_eff)^{-1} R0-,
+  // the Lehmann sums of App. C over the eigenpairs of each H_eff
   const double E0 = c->gs_E0;
-  for (int iz = 0; iz < nz; ++iz) {
-    for (int a = 0; a < L; ++a)
-      for (int b = 0; b < L; ++b) {
-        double re = 0.0, im = 0.0;
-        for (int side = 0; side < 2; ++side) {
-          const BandRun& R = side == 0 ? plus : minus;
-          for (int m = 0; m < R.K; ++m) {
-            const double q = R.Q[size_t(a) * R.K + m] * R.Q[size_t(b) * R.K + m];
-            if (q == 0.0) continue;
-            const double dr = side == 0 ? z_re[iz] + E0 - R.E[m] : z_re[iz] - E0 + R.E[m];
-            const double di = z_im[iz];
-            const double d2 = dr * dr + di * di;
-            re += q * dr / d2;
-            im -= q * di / d2;
-          }
-        }
-        G_re[(size_t(iz) * L + a) * L + b] = re;
-        G_im[(size_t(iz) * L + a) * L + b] = im;
-      }
-  }
+  std::fill(G_re, G_re + size_t(nz) * L * L, 0.0);
+  std::fill(G_im, G_im + size_t(nz) * L * L, 0.0);
+  if (!band_resolvent(plus, L, E0, true, z_re, z_im, nz, G_re, G_im) ||
+      !band_resolvent(minus, L, E0, false, z_re, z_im, nz, G_re, G_im))
+    return fail(c, MCD_E_BREAKDOWN, "band Lanczos: singular block of z - H_eff");
   return MCD_OK;
 }
 
@@ -874,9 +1350,11 @@ int green_gradient(mcd_ctx* c, const int* site, const int* spin, int L, int n_bl
   std::vector<double> psi, kc;
   std::vector<int64_t> keep;
   std::vector<uint64_t> kw;
-  double kn = 0.0;
-  st = kept_ground_state(c, w_t, psi, keep, kw, kc, kn);
+  KeptDev kd;
+  st = kept_ground_state_dev(c, w_t, kd);
+  if (st == MCD_OK) st = kept_to_host(c, kd, psi, keep, kw, kc);
   if (st != MCD_OK) return st;
+  const double kn = kd.kn;
   const int n = c->n;
   const int64_t N = c->idx.n, nk = int64_t(keep.size());
   cudaStream_t s = c->stream;
@@ -892,12 +1370,13 @@ int green_gradient(mcd_ctx* c, const int* site, const int* spin, int L, int n_bl
   gs.gu.assign(n, 0.0);
   double* buf = nullptr;   // d_r [nk] | b, lam, r, p, q, u [N each] | partials [kParts]
   const int kParts = device_sms() * 4;
-  cudaError_t e = cudaMalloc(&buf, sizeof(double) * (size_t(nk) + 6 * size_t(N) + kParts));
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), sizeof(double) * (size_t(nk) + 6 * size_t(N) + kParts), s);
   if (e != cudaSuccess) return fail(c, MCD_E_OOM, "Green gradient: work vectors");
   struct Free {
     double* p;
-    ~Free() { cudaFree(p); }
-  } guard{buf};
+    cudaStream_t s;
+    ~Free() { cudaFreeAsync(p, s); }
+  } guard{buf, s};
   gs.d_r = buf;
   double* vb = buf + nk;
   double* lam = vb + N;
@@ -909,8 +1388,8 @@ int green_gradient(mcd_ctx* c, const int* site, const int* spin, int L, int n_bl
   e = cudaMemsetAsync(buf, 0, sizeof(double) * (size_t(nk) + 6 * size_t(N)), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "Green gradient: clear");
   BandRun plus, minus;
-  st = one_side<double>(c, kw, kc, site, spin, L, true, n_blocks, plus, &gs);
-  if (st == MCD_OK) st = one_side<double>(c, kw, kc, site, spin, L, false, n_blocks, minus, &gs);
+  st = one_side<double>(c, kd.words, kd.coef, kd.n, site, spin, L, true, n_blocks, plus, &gs);
+  if (st == MCD_OK) st = one_side<double>(c, kd.words, kd.coef, kd.n, site, spin, L, false, n_blocks, minus, &gs);
   if (st != MCD_OK) return st;
   // start-vector term through the renormalised truncation, on the full basis
   std::vector<double> rk(nk), b(N, 0.0);

@@ -23,6 +23,7 @@
 // The fp32 form ends, like the single-instance one, with the fp64 Rayleigh
 // quotient of each instance's Ritz vector.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -454,7 +455,7 @@ class Batch {
     a.nw = nw_;
     a.xs_cap = xs_cap<T>();
     const size_t smem = smem_bytes<T>();
-    static bool configured = false;
+    static std::atomic<bool> configured{false};
     if (!configured) {
       cudaFuncSetAttribute(batch_hv_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       cudaFuncSetAttribute(batch_hv_kernel<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -687,7 +688,10 @@ int Batch::lanczos(int max_iter, double tol, uint64_t seed, double* E0, int* ite
     if (bad_of[i]) status = MCD_E_BREAKDOWN;
     else if (!conv[i] && tol > 0 && status == MCD_OK) status = MCD_E_NOT_CONVERGED;
   }
-  if (fp32 || psi) {
+  {
+    // the fp64 Ritz vector of every instance: its Rayleigh quotient (fp32
+    // form), the caller's psi, and the ground state each context keeps for
+    // the Green function (as mcd_lanczos_ground keeps it)
     std::vector<double> cf(size_t(cap) * n_, 0.0);
     for (int i = 0; i < n_; ++i)
       for (int j = 0; j < m_of[i]; ++j) cf[size_t(i) * cap + j] = evs[i][j] / std::sqrt(hn[size_t(i) * cap + j]);
@@ -721,9 +725,35 @@ int Batch::lanczos(int max_iter, double tol, uint64_t seed, double* E0, int* ite
       sc[i] = 1.0 / std::sqrt(hdots[i]);
       if (fp32) e0[i] = hdots[n_ + i] / hdots[i];
     }
+    e = cudaMemcpyAsync(scale.p, sc.data(), sizeof(double) * n_, cudaMemcpyHostToDevice, s_);
+    if (e != cudaSuccess) return cuda_fail(c0_, e, "batch psi");
+    {
+      DevPtr g64;
+      e = g64.alloc(sizeof(double) * ntot_);
+      if (e != cudaSuccess) return cuda_fail(c0_, e, "batch ground states");
+      bcast_kernel<double><<<egrid(ntot_), kBT, 0, s_>>>(g64.as<double>(), psi64.as<double>(), ntot_,
+                                                         scale.as<double>(), offd_.as<int64_t>(), n_);
+      MCD_LAUNCHED(c0_);
+      for (int i = 0; i < n_ && e == cudaSuccess; ++i) {
+        mcd_ctx* c = ctxs_[i];
+        const int64_t ni = off_[i + 1] - off_[i];
+        c->gs_valid = false;
+        if (!c->gs_psi || c->gs_n != ni) {
+          if (c->gs_psi) cudaFreeAsync(c->gs_psi, s_);
+          c->gs_psi = nullptr;
+          e = cudaMallocAsync(reinterpret_cast<void**>(&c->gs_psi), sizeof(double) * size_t(ni), s_);
+          if (e != cudaSuccess) break;
+          c->gs_n = ni;
+        }
+        e = cudaMemcpyAsync(c->gs_psi, g64.as<double>() + off_[i], sizeof(double) * size_t(ni),
+                            cudaMemcpyDeviceToDevice, s_);
+        c->gs_E0 = e0[i];
+        c->gs_valid = !bad_of[i];
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s_);   // g64 is freed on return
+      if (e != cudaSuccess) return cuda_fail(c0_, e, "batch ground states");
+    }
     if (psi) {
-      e = cudaMemcpyAsync(scale.p, sc.data(), sizeof(double) * n_, cudaMemcpyHostToDevice, s_);
-      if (e != cudaSuccess) return cuda_fail(c0_, e, "batch psi");
       // normalised Ritz vector of each instance into the caller's buffers
       DevPtr out;
       e = out.alloc(sizeof(T) * ntot_);

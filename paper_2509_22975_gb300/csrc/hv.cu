@@ -17,6 +17,7 @@
 // targets are broadcast within the group by shuffles, then every lane
 // gathers its column chunk of the target row (coalesced 16-byte loads when
 // the rows are aligned).
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 
@@ -1056,7 +1057,7 @@ cudaError_t launch_pair(mcd_ctx* c, const void* x, void* y, int ncols, int ld, d
     a.xs_cap = int(kStageXBytes / sizeof(T));
     smem = size_t(a.off_xs) + kStageXBytes;
   }
-  static int configured_smem = -1;   // per instantiation; one device per process in practice
+  static std::atomic<int> configured_smem{-1};   // per instantiation; one device per process in practice
   if (configured_smem < int(smem)) {
     if (bitmap) {
       cudaFuncSetAttribute(hv_bitmap_kernel<T, VEC, G, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -1078,7 +1079,7 @@ cudaError_t launch_pair(mcd_ctx* c, const void* x, void* y, int ncols, int ld, d
     a.off_xs = (a.off_bm + 8 * a.nw + 15) & ~15;
     smem = size_t(a.off_xs) + kStageX1Bytes;
     a.xs_cap = int(kStageX1Bytes / sizeof(T));
-    static int configured_l1 = -1;
+    static std::atomic<int> configured_l1{-1};
     if (configured_l1 < int(smem)) {
       cudaFuncSetAttribute(hv_l1_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       cudaFuncSetAttribute(hv_l1_kernel<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -1117,7 +1118,7 @@ cudaError_t launch_pair(mcd_ctx* c, const void* x, void* y, int ncols, int ld, d
     const int xs_bytes = std::max(1024, kStageXcBytes - a.off_xs) & ~15;
     smem = size_t(a.off_xs) + xs_bytes;
     a.xs_cap = int(xs_bytes / sizeof(T));
-    static int configured_lc = -1;
+    static std::atomic<int> configured_lc{-1};
     if (configured_lc < int(smem)) {
       cudaFuncSetAttribute(hv_lc_kernel<T, VEC, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       cudaFuncSetAttribute(hv_lc_kernel<T, VEC, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

@@ -41,7 +41,9 @@
 // Many columns (band Lanczos): CTAs stage x rows of an item with ordinary
 // loads and groups of G lanes share a state; with G > 1, pass B reads a
 // dn-major copy of X.
+#include <atomic>
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "hv_cache.cuh"
@@ -693,9 +695,11 @@ int build_layout(mcd_ctx* c, Layout& L, const LayoutItems& li, const std::vector
   cc.n_items = int64_t(li.items.size());
   cc.n_slices = n_slices;
   cc.max_stage = li.max_stage;
-  cc.stage_rows.resize(li.items.size());
-  for (size_t i = 0; i < li.items.size(); ++i) cc.stage_rows[i] = li.items[i].se - li.items[i].sb;
+  std::vector<uint2>& rng = c->stage_range[&L == &c->idx.B ? 0 : 1];
+  rng.resize(li.items.size());
+  for (size_t i = 0; i < li.items.size(); ++i) rng[i] = make_uint2(li.items[i].sb, li.items[i].se);
   cc.units_key = -1;
+  std::memset(c->cols_pick, 0, sizeof(c->cols_pick));   // a new basis or Hamiltonian: pick again
   cc.n_cls = int(coef.size());
   const int nc1 = std::max(cc.n_cls, 1);
   cudaError_t e = grow(cc.items, cc.items_cap, cc.n_items, sizeof(CItem), s);
@@ -869,7 +873,7 @@ template <typename T>
 cudaError_t launch_stream(mcd_ctx* c, const void* x, void* y, double* partials, int max_parts, unsigned int* ticket,
                           double* dot_out) {
   const int smem = kSStages * kSStageBytes + cls_bytes(c);
-  static int configured = -1;   // per instantiation
+  static std::atomic<int> configured{-1};   // per instantiation
   if (configured < smem) {
     cudaFuncSetAttribute(hv_stream_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(hv_stream_kernel<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -955,9 +959,9 @@ void cache_invalidate(Layout& L) {
   L.cc.failed = 0;
 }
 
-void free_cache(Layout& L) {
+void free_cache(Layout& L, cudaStream_t s) {
   ConnCache& cc = L.cc;
-  auto f = [](void* p) { if (p) cudaFree(p); };
+  auto f = [s](void* p) { if (p) cudaFreeAsync(p, s); };
   f(cc.items); f(cc.col); f(cc.smap); f(cc.rec); f(cc.c64); f(cc.xb); f(cc.yb); f(cc.xbm); f(cc.units);
   cc = ConnCache();
 }

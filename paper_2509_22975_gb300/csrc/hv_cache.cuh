@@ -80,7 +80,7 @@ struct CArgs {
   unsigned int* ticket;
   double* dot_out;
   unsigned int* err;
-  const uint2* units;            // many-column kernel: {item, col0 | G << 16 | x in global memory << 24}
+  const uint4* units;            // many-column kernel: {first item, sb, stage rows, col0 | G | flags | items}
   int64_t n_units;
   uint32_t spin_limit;           // polls of an mbarrier before a wait gives up
   int64_t withhold;              // time-out test: item whose copies are not issued (-1 none)

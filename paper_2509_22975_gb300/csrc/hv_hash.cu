@@ -34,6 +34,7 @@
 //
 // Filter bits and table slots are set by atomics in whatever order threads
 // arrive, but a word has one position, so results do not depend on it.
+#include <atomic>
 #include <algorithm>
 #include <vector>
 
@@ -706,26 +707,26 @@ cudaError_t build_hash(mcd_ctx* c, Layout& L, int hcap) {
   flush(L.nblk);
   if (tab_len > 0xFFFFFFFFll || flt_len > 0xFFFFFFFFll) return cudaErrorInvalidValue;
   if (int64_t(items.size()) > L.hitem_cap) {
-    if (L.hitems) cudaFree(L.hitems);
+    if (L.hitems) cudaFreeAsync(L.hitems, c->stream);
     L.hitems = nullptr;
     L.hitem_cap = 0;
-    e = cudaMalloc(&L.hitems, items.size() * sizeof(HItem));
+    e = cudaMallocAsync(&L.hitems, items.size() * sizeof(HItem), c->stream);
     if (e != cudaSuccess) return e;
     L.hitem_cap = int64_t(items.size());
   }
   if (tab_len > L.htab_cap) {
-    if (L.htab) cudaFree(L.htab);
+    if (L.htab) cudaFreeAsync(L.htab, c->stream);
     L.htab = nullptr;
     L.htab_cap = 0;
-    e = cudaMalloc(&L.htab, size_t(tab_len) * 4);
+    e = cudaMallocAsync(&L.htab, size_t(tab_len) * 4, c->stream);
     if (e != cudaSuccess) return e;
     L.htab_cap = tab_len;
   }
   if (flt_len > L.hflt_cap) {
-    if (L.hflt) cudaFree(L.hflt);
+    if (L.hflt) cudaFreeAsync(L.hflt, c->stream);
     L.hflt = nullptr;
     L.hflt_cap = 0;
-    e = cudaMalloc(&L.hflt, size_t(flt_len) * 4);
+    e = cudaMallocAsync(&L.hflt, size_t(flt_len) * 4, c->stream);
     if (e != cudaSuccess) return e;
     L.hflt_cap = flt_len;
   }
@@ -783,7 +784,7 @@ cudaError_t launch_hash1(mcd_ctx* c, const void* x, void* y, int ld, double* par
   a.ticket = ticket;
   a.dot_out = dot_out;
   const size_t smem = item_smem(a, sizeof(T));
-  static int configured = -1;
+  static std::atomic<int> configured{-1};
   if (configured < int(smem)) {
     cudaFuncSetAttribute(hv_hash1_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     cudaFuncSetAttribute(hv_hash1_kernel<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -821,7 +822,7 @@ template <typename T, int VEC, int G>
 cudaError_t launch_hashm(mcd_ctx* c, const void* x, void* y, int ncols, int ld) {
   HvArgs a = hash_args(c, x, y, ncols, ld);
   const size_t smem = item_smem(a, 0);
-  static int configured = -1;
+  static std::atomic<int> configured{-1};
   if (configured < int(smem)) {
     cudaFuncSetAttribute(hv_hashm_kernel<T, VEC, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     cudaFuncSetAttribute(hv_hashm_kernel<T, VEC, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -866,10 +867,10 @@ bool hash_eligible(const mcd_ctx* c) {
   return c->hp->n_hg > 0 && (c->hv_algo == 3 || (c->hv_algo == 0 && c->n > 16));
 }
 
-void free_hash(Layout& L) {
-  if (L.hitems) cudaFree(L.hitems);
-  if (L.htab) cudaFree(L.htab);
-  if (L.hflt) cudaFree(L.hflt);
+void free_hash(Layout& L, cudaStream_t s) {
+  if (L.hitems) cudaFreeAsync(L.hitems, s);
+  if (L.htab) cudaFreeAsync(L.htab, s);
+  if (L.hflt) cudaFreeAsync(L.hflt, s);
   L.hitems = nullptr;
   L.htab = nullptr;
   L.hflt = nullptr;

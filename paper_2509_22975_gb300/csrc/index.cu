@@ -187,7 +187,8 @@ __global__ void check_basis_kernel(const uint64_t* w, int64_t n, int nsites, int
 
 struct DevBuf {
   void* p = nullptr;
-  ~DevBuf() { if (p) cudaFree(p); }
+  cudaStream_t s = nullptr;
+  ~DevBuf() { if (p) cudaFreeAsync(p, s); }
 };
 
 int grid_of(int64_t n, int t) { return int((n + t - 1) / t); }
@@ -242,13 +243,13 @@ static cudaError_t build_layout(mcd_ctx* c, const uint32_t* major, int64_t n, La
   return cudaGetLastError();
 }
 
-void free_index(DevIndex& ix) {
-  auto f = [](void* p) { if (p) cudaFree(p); };
+void free_index(DevIndex& ix, cudaStream_t s) {
+  auto f = [s](void* p) { if (p) cudaFreeAsync(p, s); };
   f(ix.words);
   for (Layout* L : {&ix.A, &ix.B}) {
     f(L->minor); f(L->blk_off); f(L->blk_major); f(L->item_blk); f(L->perm);
-    free_hash(*L);
-    free_cache(*L);
+    free_hash(*L, s);
+    free_cache(*L, s);
     *L = Layout();
   }
   ix.words = nullptr;
@@ -258,22 +259,22 @@ void free_index(DevIndex& ix) {
 }
 
 // Persistent index buffers sized for `cap` states; kept across bases that fit.
-static cudaError_t reserve_index(DevIndex& ix, int64_t n) {
+static cudaError_t reserve_index(DevIndex& ix, int64_t n, cudaStream_t s) {
   if (ix.cap >= n && ix.words) return cudaSuccess;
-  free_index(ix);
+  free_index(ix, s);
   const int64_t items = (n + kItem - 1) / kItem + 1;
   // words and perm end 16 bytes past the last state: the streaming H~v kernel
   // copies aligned 16-byte units that cover a range of states
-  cudaError_t e = cudaMalloc(&ix.words, (n + 2) * sizeof(uint64_t));
+  cudaError_t e = cudaMallocAsync(&ix.words, (n + 2) * sizeof(uint64_t), s);
   for (Layout* L : {&ix.A, &ix.B}) {
-    if (e == cudaSuccess) e = cudaMalloc(&L->minor, n * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&L->blk_off, (n + 1) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&L->blk_major, n * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&L->item_blk, items * 4);
+    if (e == cudaSuccess) e = cudaMallocAsync(&L->minor, n * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&L->blk_off, (n + 1) * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&L->blk_major, n * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&L->item_blk, items * 4, s);
   }
-  if (e == cudaSuccess) e = cudaMalloc(&ix.B.perm, (n + 4) * 4);
+  if (e == cudaSuccess) e = cudaMallocAsync(&ix.B.perm, (n + 4) * 4, s);
   if (e != cudaSuccess) {
-    free_index(ix);
+    free_index(ix, s);
     return e;
   }
   ix.cap = n;
@@ -286,14 +287,14 @@ int build_index(mcd_ctx* c, const uint64_t* words, int64_t n, bool on_device) {
   DevIndex& ix = c->idx;
   cudaStream_t s = c->stream;
   const int T = 256;
-  e = reserve_index(ix, n);
+  e = reserve_index(ix, n, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(index)");
   ix.n = n;
   ix.nnz = -1;
   e = cudaMemcpyAsync(ix.words, words, n * sizeof(uint64_t),
                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) {
-    free_index(ix);
+    free_index(ix, s);
     return cuda_fail(c, e, "copy words");
   }
   {
@@ -309,15 +310,15 @@ int build_index(mcd_ctx* c, const uint64_t* words, int64_t n, bool on_device) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFreeAsync(bad, s);
     if (e != cudaSuccess) {
-      free_index(ix);
+      free_index(ix, s);
       return cuda_fail(c, e, "basis check");
     }
     if (hbad & 1u) {
-      free_index(ix);
+      free_index(ix, s);
       return fail(c, MCD_E_INVALID, "basis words must be strictly ascending");
     }
     if (hbad & 2u) {
-      free_index(ix);
+      free_index(ix, s);
       return fail(c, MCD_E_SECTOR, "word outside the (N_up, N_dn) sector");
     }
   }
@@ -378,7 +379,7 @@ int build_index(mcd_ctx* c, const uint64_t* words, int64_t n, bool on_device) {
   cudaFreeAsync(k2, s); cudaFreeAsync(v2, s); cudaFreeAsync(hist, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    free_index(ix);
+    free_index(ix, s);
     return cuda_fail(c, e, "index build");
   }
   return MCD_OK;

@@ -437,9 +437,9 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
   *resid_out = std::sqrt(rr / nn);
   // keep the normalised ground state for the Green function
   if (!c->gs_psi || c->gs_n != n) {
-    if (c->gs_psi) cudaFree(c->gs_psi);
+    if (c->gs_psi) cudaFreeAsync(c->gs_psi, s);
     c->gs_psi = nullptr;
-    e = cudaMalloc(&c->gs_psi, sizeof(double) * n);
+    e = cudaMallocAsync(&c->gs_psi, sizeof(double) * n, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "ground-state copy");
     c->gs_n = n;
   }

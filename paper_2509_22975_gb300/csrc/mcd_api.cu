@@ -5,7 +5,9 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <thread>
 
 #include "mcd_internal.h"
 
@@ -78,6 +80,75 @@ int install_basis(mcd_ctx* c, std::vector<uint64_t>&& words) {
 
 }  // namespace
 
+namespace {
+
+// f(i, ctx) for every instance, on a pool of host threads: each thread owns a
+// non-blocking CUDA stream that it sets on the instance's context for the
+// call (the context's stream is restored afterwards), so instances run
+// concurrently on the GPU.  Returns the status of the first failing instance
+// (lowest index), its message in ctxs[0]'s last error.
+template <typename F>
+int run_instances(mcd_ctx* const* ctxs, int n, F f) {
+  const int hw = int(std::thread::hardware_concurrency());
+  const int nthreads = std::max(1, std::min(n, std::min(hw > 0 ? hw : 1, 16)));
+  std::atomic<int> next{0};
+  std::mutex mu;
+  int err_idx = -1, err_st = MCD_OK;
+  std::string err_msg;
+  auto note = [&](int i, int st, const std::string& msg) {
+    std::lock_guard<std::mutex> lock(mu);
+    if (err_idx < 0 || i < err_idx) {
+      err_idx = i;
+      err_st = st;
+      err_msg = msg;
+    }
+  };
+  auto worker = [&]() {
+    cudaSetDevice(ctxs[0]->device);
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      note(0, MCD_E_CUDA, std::string("batch stream: ") + cudaGetErrorString(e));
+      return;
+    }
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n) break;
+      mcd_ctx* c = ctxs[i];
+      cudaStream_t old = c->stream;
+      int st = mcd_set_stream(c, s);
+      if (st == MCD_OK) st = f(i, c);
+      const std::string msg = c->err;
+      const int st2 = mcd_set_stream(c, old);   // waits for this instance's work
+      if (st == MCD_OK) st = st2;
+      if (st != MCD_OK) note(i, st, msg);
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> pool;
+  pool.reserve(nthreads);
+  for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  if (err_idx >= 0) return fail(ctxs[0], err_st, "instance " + std::to_string(err_idx) + ": " + err_msg);
+  return MCD_OK;
+}
+
+int check_instances(mcd_ctx* const* ctxs, int n, bool same_sites) {
+  if (!ctxs || n < 1 || !ctxs[0]) return MCD_E_INVALID;
+  for (int i = 0; i < n; ++i) {
+    mcd_ctx* c = ctxs[i];
+    if (!c) return fail(ctxs[0], MCD_E_INVALID, "batch: null context");
+    if (c->device != ctxs[0]->device) return fail(ctxs[0], MCD_E_INVALID, "batch: contexts on different devices");
+    if (same_sites && c->n != ctxs[0]->n) return fail(ctxs[0], MCD_E_INVALID, "batch: instances differ in sites");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(ctxs[0], MCD_E_INVALID, "batch: a context appears twice");
+  }
+  return MCD_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int mcd_create(mcd_ctx** out, int device, void* cuda_stream) {
@@ -128,13 +199,16 @@ int mcd_destroy(mcd_ctx* c) {
   if (has_device(c)) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    free_index(c->idx);
+    free_index(c->idx, c->stream);
     free_lanczos(c->lw);
-    if (c->d_eps) cudaFree(c->d_eps);
-    if (c->d_U) cudaFree(c->d_U);
-    if (c->d_pclass) cudaFree(c->d_pclass);
-    if (c->gs_psi) cudaFree(c->gs_psi);
-    if (c->tm) {
+    if (c->d_eps) cudaFreeAsync(c->d_eps, c->stream);
+    if (c->d_U) cudaFreeAsync(c->d_U, c->stream);
+    if (c->d_pclass) cudaFreeAsync(c->d_pclass, c->stream);
+    if (c->gs_psi) cudaFreeAsync(c->gs_psi, c->stream);
+    cudaStreamSynchronize(c->stream);
+    for (auto& ev : c->tune_ev)
+      if (ev) cudaEventDestroy(ev);
+    if (c->tm && !c->tm_borrowed) {
       if (c->tm->created)
         for (auto& ev : c->tm->ev) cudaEventDestroy(ev);
       delete c->tm;
@@ -147,7 +221,15 @@ int mcd_destroy(mcd_ctx* c) {
 
 int mcd_set_stream(mcd_ctx* c, void* stream) {
   if (!c) return MCD_E_INVALID;
-  c->stream = static_cast<cudaStream_t>(stream);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (has_device(c) && s != c->stream) {
+    // the context's buffers are allocated and freed in the order of its
+    // stream: the old stream's work completes before the new one is used
+    cudaSetDevice(c->device);
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronise the previous stream");
+  }
+  c->stream = s;
   return MCD_OK;
 }
 
@@ -187,6 +269,10 @@ int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
       if (value < 0 || value > 1) return fail(c, MCD_E_INVALID, "KRYLOV_STORE must be 0 or 1");
       c->krylov_store = int(value);
       return MCD_OK;
+    case MCD_OPT_HV_COLS:
+      if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "HV_COLS must be 0, 1 or 2");
+      c->hv_cols = int(value);
+      return MCD_OK;
     case MCD_OPT_APPLY_SYNC:
       if (value < 0 || value > 1) return fail(c, MCD_E_INVALID, "APPLY_SYNC must be 0 or 1");
       c->apply_sync = int(value);
@@ -199,8 +285,8 @@ int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
       if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "HV_CACHE must be 0, 1 or 2");
       c->hv_cache = int(value);
       if (value == 1 && has_device(c)) {   // release the records
-        free_cache(c->idx.A);
-        free_cache(c->idx.B);
+        free_cache(c->idx.A, c->stream);
+        free_cache(c->idx.B, c->stream);
       }
       return MCD_OK;
     case MCD_OPT_SAMPLER_THREADS:
@@ -337,12 +423,14 @@ int mcd_set_hamiltonian(mcd_ctx* c, int n, const double* t, const double* eps, c
     int st = need_device(c);
     if (st != MCD_OK) return st;
     if (!c->d_eps) {
-      cudaError_t er = cudaMalloc(&c->d_eps, sizeof(double) * kMaxSites);
-      if (er == cudaSuccess) er = cudaMalloc(&c->d_U, sizeof(double) * kMaxSites);
+      cudaError_t er = cudaMallocAsync(&c->d_eps, sizeof(double) * kMaxSites, c->stream);
+      if (er == cudaSuccess) er = cudaMallocAsync(&c->d_U, sizeof(double) * kMaxSites, c->stream);
       if (er != cudaSuccess) return cuda_fail(c, er, "cudaMalloc(eps, U)");
     }
-    cudaError_t er = cudaMemcpy(c->d_eps, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
-    if (er == cudaSuccess) er = cudaMemcpy(c->d_U, u.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    cudaError_t er = cudaMemcpyAsync(c->d_eps, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+    if (er == cudaSuccess)
+      er = cudaMemcpyAsync(c->d_U, u.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+    if (er == cudaSuccess) er = cudaStreamSynchronize(c->stream);   // e, u are locals
     if (er != cudaSuccess) return cuda_fail(c, er, "copy eps, U");
     hp.eps = c->d_eps;
     hp.U = c->d_U;
@@ -409,11 +497,13 @@ int mcd_set_hamiltonian(mcd_ctx* c, int n, const double* t, const double* eps, c
           hp.pcls_hi[cc] = float(amp[cc]);
           hp.pcls_lo[cc] = float(amp[cc] - double(hp.pcls_hi[cc]));
         }
-        if (c->d_pclass) cudaFree(c->d_pclass);
+        if (c->d_pclass) cudaFreeAsync(c->d_pclass, c->stream);
         c->d_pclass = nullptr;
-        cudaError_t er2 = cudaMalloc(&c->d_pclass, tab.size() * sizeof(uint2));
+        cudaError_t er2 = cudaMallocAsync(&c->d_pclass, tab.size() * sizeof(uint2), c->stream);
         if (er2 == cudaSuccess)
-          er2 = cudaMemcpy(c->d_pclass, tab.data(), tab.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+          er2 = cudaMemcpyAsync(c->d_pclass, tab.data(), tab.size() * sizeof(uint2), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (er2 == cudaSuccess) er2 = cudaStreamSynchronize(c->stream);   // tab is a local
         if (er2 != cudaSuccess) return cuda_fail(c, er2, "partner tables");
         hp.ptab = static_cast<const uint2*>(c->d_pclass);
         hp.pflip = hp.ptab + size_t(ng) * 512;
@@ -427,7 +517,7 @@ int mcd_set_hamiltonian(mcd_ctx* c, int n, const double* t, const double* eps, c
   if (sector_changed) {
     c->basis.clear();
     c->n_basis = 0;
-    if (has_device(c)) free_index(c->idx);
+    if (has_device(c)) free_index(c->idx, c->stream);
     free_lanczos(c->lw);
   }
   c->idx.nnz = -1;
@@ -688,6 +778,37 @@ int mcd_green_gradient(mcd_ctx* c, const int* site, const int* spin, int L, int 
   } catch (const std::bad_alloc&) {
     return fail(c, MCD_E_OOM, "Green gradient: out of host memory");
   }
+}
+
+int mcd_batch_band_lanczos_green(mcd_ctx* const* ctxs, int n_inst, const int* site, const int* spin, int L,
+                                 int n_block_iter, double w_t, int dtype, const double* z_re, const double* z_im,
+                                 int nz, double* G_re, double* G_im, int64_t* dim_plus, int64_t* dim_minus) {
+  int st = check_instances(ctxs, n_inst, false);
+  if (st != MCD_OK) return st;
+  if (nz < 0 || (nz > 0 && (!G_re || !G_im))) return fail(ctxs[0], MCD_E_INVALID, "null argument");
+  const size_t per = size_t(nz) * size_t(std::max(L, 0)) * size_t(std::max(L, 0));
+  return run_instances(ctxs, n_inst, [&](int i, mcd_ctx* c) {
+    return mcd_band_lanczos_green(c, site, spin, L, n_block_iter, w_t, dtype, z_re, z_im, nz,
+                                  G_re ? G_re + per * i : nullptr, G_im ? G_im + per * i : nullptr,
+                                  dim_plus ? dim_plus + i : nullptr, dim_minus ? dim_minus + i : nullptr);
+  });
+}
+
+int mcd_batch_green_gradient(mcd_ctx* const* ctxs, int n_inst, const int* site, const int* spin, int L,
+                             int n_block_iter, double w_t, const double* z_re, const double* z_im, int nz,
+                             const double* g_re, const double* g_im, double cg_tol, double* grad_t,
+                             double* grad_eps, double* grad_U, int* cg_iters) {
+  int st = check_instances(ctxs, n_inst, true);
+  if (st != MCD_OK) return st;
+  if (!g_re || !g_im || !grad_t || !grad_eps || !grad_U || nz < 1)
+    return fail(ctxs[0], MCD_E_INVALID, "null argument");
+  const int n = ctxs[0]->n;
+  const size_t per = size_t(nz) * size_t(std::max(L, 0)) * size_t(std::max(L, 0));
+  return run_instances(ctxs, n_inst, [&](int i, mcd_ctx* c) {
+    return mcd_green_gradient(c, site, spin, L, n_block_iter, w_t, z_re, z_im, nz, g_re + per * i, g_im + per * i,
+                              cg_tol, grad_t + size_t(n) * n * i, grad_eps + size_t(n) * i, grad_U + size_t(n) * i,
+                              cg_iters ? cg_iters + i : nullptr);
+  });
 }
 
 int mcd_symeig(int n, const double* A, double* w, int rows, double* X) {

@@ -132,10 +132,10 @@ struct ConnCache {
   void* yb = nullptr;            // pass B's part of y (streaming kernels), read by pass A
   unsigned int* err = nullptr;   // set by a kernel whose bounded wait ran out
   int64_t items_cap = 0, col_cap = 0, smap_cap = 0, rec_cap = 0, cls_cap = 0, xb_cap = 0, yb_cap = 0, xbm_cap = 0;
-  // many-column kernel: stage rows (se - sb) of each item (host), and the work
-  // units (item, column tile) of the last column count and element size
-  std::vector<uint32_t> stage_rows;
-  uint2* units = nullptr;
+  // many-column kernel: work units (items of one stage range, column tile)
+  // of the last column count and element size (the items' stage ranges are
+  // kept on the host in mcd_ctx::stage_range)
+  uint4* units = nullptr;
   int64_t n_units = 0, units_cap = 0;
   int units_key = -1;            // ncp * 16 + element size of `units` (-1 none)
 };
@@ -232,13 +232,19 @@ struct mcd_ctx {
   int sampler_threads = 0;
   int sampler_where = 0;                // 0 auto, 1 host threads, 2 device
   int hv_cache = 0;                     // 0 auto, 1 off, 2 required
+  std::vector<uint2> stage_range[2];    // connection cache: stage range {sb, se} of each item, layouts B and A
   int krylov_store = 0;                 // 0 auto, 1 always regenerate the Lanczos vectors
   int apply_sync = 1;                   // mcd_apply waits and reads the wait-error words
+  int hv_cols = 0;                      // many-column kernel: 0 timed pick, 1 pipelined tiles, 2 CTA per item
+  int cols_pick[65][2] = {};            // timed pick per column count (<= 64) and dtype: 0 none, 1 tiles, 2 items
+  cudaEvent_t tune_ev[3] = {nullptr, nullptr, nullptr};
   int64_t wait_test_item = -1;          // one-shot: withhold this item's copies (time-out test)
   mcd::Timing* tm = nullptr;
+  bool tm_borrowed = false;             // tm belongs to another context (band Lanczos runs)
 };
 
 namespace mcd {
+
 
 // streaming multiprocessors of the current device (queried once per device)
 int device_sms();
@@ -271,6 +277,10 @@ int band_lanczos_green(mcd_ctx* c, const int* site, const int* spin, int L, int 
 // device sampler (sampler_gpu.cu): same result as sample_basis; applies when
 // every nonzero U_i has the same value; installs the basis on the device
 bool device_sampler_eligible(const mcd_ctx* c);
+// keys[0, n) sorted in place on their low `bits` bits, *out = the distinct
+// keys in ascending order (*nout of them; stream-ordered allocation on the
+// context's stream that the caller frees with cudaFreeAsync)
+int sort_unique_device(mcd_ctx* c, uint64_t* keys, int64_t n, int bits, uint64_t** out, int64_t* nout);
 int sample_basis_device(mcd_ctx* c, uint64_t seed, int64_t n_target, double beta, const uint64_t* seeds,
                         int64_t n_seed, int flags, int64_t* n_out);
 
@@ -288,7 +298,7 @@ int green_gradient(mcd_ctx* c, const int* site, const int* spin, int L, int n_bl
 int build_index(mcd_ctx* c, const uint64_t* words, int64_t n, bool on_device);
 // exclusive scan of n uint32 values (in may equal out), stream-ordered
 cudaError_t scan_u32(mcd_ctx* c, const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
-void free_index(DevIndex& ix);
+void free_index(DevIndex& ix, cudaStream_t s);   // stream-ordered frees on s
 
 // H*v (hv.cu)
 int hv_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype,
@@ -303,7 +313,7 @@ int hv_dot_ctas(mcd_ctx* c, int ncols, int dtype);
 bool hash_eligible(const mcd_ctx* c);
 int hash_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, double* dot_partials,
                int max_parts, unsigned int* ticket, double* dot_out);
-void free_hash(Layout& L);
+void free_hash(Layout& L, cudaStream_t s);
 
 // connection cache (hv_cache.cu): built by the first H*v of a basis (when
 // c->hv_cache allows and hv_algo == 0), then used by every H*v whose columns
@@ -311,7 +321,7 @@ void free_hash(Layout& L);
 int cache_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, double* dot_partials,
                 int max_parts, unsigned int* ticket, double* dot_out, bool* used);
 void cache_invalidate(Layout& L);
-void free_cache(Layout& L);
+void free_cache(Layout& L, cudaStream_t s);
 // *out = 1 when a bounded wait of a cached kernel gave up since the records were built
 int cache_errors(mcd_ctx* c, unsigned int* out);
 // MCD_E_TIMEOUT (and the words cleared) when a bounded wait gave up since the
@@ -320,6 +330,9 @@ int take_wait_errors(mcd_ctx* c);
 // cached H*V for many columns, or one column with a row stride (hv_cache_cols.cu);
 // *used = false when the columns' layout is not covered (the caller falls back)
 cudaError_t cache_apply_cols(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, bool* used);
+// the CTA-per-item many-column kernel (hv_cache_items.cu) and its scratch
+cudaError_t cache_apply_items(mcd_ctx* c, const void* x, void* y, int ncols, int ld, int dtype, bool* used);
+cudaError_t cache_items_prepare(mcd_ctx* c, int ncols, int dtype);
 
 // Lanczos (krylov.cu)
 int lanczos_ground(mcd_ctx* c, int max_iter, double tol, uint64_t seed, int dtype,

@@ -290,6 +290,29 @@ class DevSampler {
 
 }  // namespace
 
+int sort_unique_device(mcd_ctx* c, uint64_t* keys, int64_t n, int bits, uint64_t** out, int64_t* nout) {
+  *out = nullptr;
+  *nout = 0;
+  DevSampler ds(c);
+  cudaStream_t s = c->stream;
+  cudaError_t e = ds.sort(keys, nullptr, n, bits);
+  if (e != cudaSuccess) return cuda_fail(c, e, "sort of words");
+  Buf flag, uniq;
+  e = ds.alloc(flag, size_t(std::max<int64_t>(n, 1)) * 4);
+  if (e == cudaSuccess && n > 0) {
+    flag_unique_kernel<<<grid_for(n), kT, 0, s>>>(keys, n, flag.as<uint32_t>());
+    MCD_LAUNCHED(c);
+    e = cudaGetLastError();
+  }
+  int64_t nu = 0;
+  if (e == cudaSuccess) e = ds.compact(keys, n, flag.as<uint32_t>(), uniq, nu);
+  if (e != cudaSuccess) return cuda_fail(c, e, "unique words");
+  *out = uniq.as<uint64_t>();
+  uniq.p = nullptr;   // the caller frees it (stream-ordered)
+  *nout = nu;
+  return MCD_OK;
+}
+
 bool device_sampler_eligible(const mcd_ctx* c) {
   double u = 0.0;
   for (int i = 0; i < c->n; ++i) {

@@ -250,3 +250,29 @@ def test_single_column_basis_size_not_a_multiple_of_four(cut):
         check(ctx, P, w.lat.t, 1, dtype, seed=cut)
     info = ctx.mcd_hv_cache_info()
     assert info["n_conn"] == P.nnz_offdiag() and info["wait_errors"] == 0
+
+
+@pytest.mark.parametrize("name,nf", [("tilted12_u8", 1 << 16), ("square16_u8", 200000), ("rect24_u8", 60000)])
+def test_both_many_column_kernels_and_the_timed_pick(name, nf):
+    # the pipelined-tile kernel and the CTA-per-item kernel, each forced,
+    # against the oracle for 2, 8, 24 and 48 columns in fp32 and fp64; the
+    # timed pick (default) gives bit for bit what the kernel it keeps gives
+    w = getattr(C, name)()
+    ctx = device_ctx(w, nf=nf)
+    ctx.mcd_set_option(pkg.MCD_OPT_HV_CACHE, pkg.CACHE_REQUIRED)
+    B = ctx.mcd_get_basis()
+    P = H.build(model(w), B)
+    for mode in (pkg.HV_COLS_TILES, pkg.HV_COLS_ITEMS):
+        ctx.mcd_set_option(pkg.MCD_OPT_HV_COLS, mode)
+        for dt in (np.float64, np.float32):
+            for nc in (2, 8, 24, 48):
+                check(ctx, P, w.lat.t, nc, dt, seed=nc + mode)
+    X = random_block(len(B), 24, 7, np.float32)
+    ys = {}
+    for mode in (pkg.HV_COLS_AUTO, pkg.HV_COLS_TILES, pkg.HV_COLS_ITEMS):
+        ctx.mcd_set_option(pkg.MCD_OPT_HV_COLS, mode)
+        ys[mode] = [apply(ctx, X) for _ in range(2)]   # auto: the first call times both, the second uses the pick
+    assert np.array_equal(ys[pkg.HV_COLS_TILES][0], ys[pkg.HV_COLS_TILES][1])
+    assert np.array_equal(ys[pkg.HV_COLS_ITEMS][0], ys[pkg.HV_COLS_ITEMS][1])
+    picked = ys[pkg.HV_COLS_AUTO][1]
+    assert np.array_equal(picked, ys[pkg.HV_COLS_TILES][0]) or np.array_equal(picked, ys[pkg.HV_COLS_ITEMS][0])

@@ -1,9 +1,9 @@
 """Time-out path of the bounded device waits of the streaming H~x kernel.
 
-A test option (MCD_OPT_WAIT_TEST) makes the next one-column cached product
-skip the producer's arrival and copies for one work item and poll each
-wait only 4096 times, so the consumer waits on that item give up: nothing
-is left in flight and no GPU fault is involved.  The library must report
+A test option (MCD_OPT_WAIT_TEST) makes the next cached product skip the
+producer's arrival for one work item (one column) or work unit (many
+columns) and poll each wait only 4096 times, so the consumer waits on it give
+up: nothing is left waiting on a copy and no GPU fault is involved.  The library must report
 MCD_E_TIMEOUT (from mcd_apply when it waits for its product, from
 mcd_lanczos_ground at its next read-back, or from the next reading call when
 mcd_apply runs asynchronously) instead of returning an incomplete y, and the
@@ -52,6 +52,22 @@ def test_apply_reports_timeout_and_recovers(ctx):
         y.fill_(0.0)
         ctx.mcd_apply(x, y)                                     # the option applied to one product
         assert torch.equal(y, ref)
+
+
+def test_many_column_apply_reports_timeout_and_recovers(ctx):
+    n = ctx.mcd_basis_info(nnz=False)["n_states"]
+    g = torch.Generator(device="cpu").manual_seed(3)
+    x = torch.randn(n, 8, generator=g, dtype=torch.float32).to(DEV)
+    y = torch.empty_like(x)
+    ctx.mcd_apply(x, y)
+    ref = y.clone()
+    ctx.mcd_set_option(pkg.MCD_OPT_WAIT_TEST, 1)
+    with pytest.raises(pkg.MCDError) as e:
+        ctx.mcd_apply(x, y)
+    assert e.value.status == pkg.MCD_E_TIMEOUT
+    y.fill_(0.0)
+    ctx.mcd_apply(x, y)
+    assert torch.equal(y, ref)
 
 
 def test_asynchronous_apply_reports_at_the_next_reading_call(ctx):
