@@ -233,6 +233,12 @@ def run_reference(args):
 
 
 def workload_config(args, reference=False):
+    if getattr(args, "workload", "square16") == "rect24":
+        return {"workload": f"rect6x4_tp-0.3_U8_Nup11_Ndn11_mcbasis{args.n_f:.0e}_lanczos{args.iters}_fp32",
+                "lattice": "6x4 periodic square, R1=(6,0) R2=(0,4), t=1, t'=-0.3", "U": 8.0, "n_up": 11,
+                "n_dn": 11, "n_f": args.n_f, "mc_beta": 0.2, "mc_seed": 0, "lanczos_steps": args.iters, "ncols": 1,
+                "vectors": "fp32 (fp64 coefficients and reductions)",
+                "parallelism": f"replicas x{args.gpus}" if not reference else "cpu"}
     return {"workload": "square4x4_tp-0.3_U8_Nup7_Ndn7_mcbasis1e7_lanczos200_fp32",
             "lattice": "4x4 periodic square, R1=(4,0) R2=(0,4), t=1, t'=-0.3", "U": 8.0, "n_up": 7, "n_dn": 7,
             "n_f": args.n_f, "mc_beta": 0.2, "mc_seed": 0, "lanczos_steps": args.iters, "ncols": 1,
@@ -302,6 +308,42 @@ def impurity_batch(pkg, dev, n_inst=256, steps=400, tol=1e-6):
                              "sequential_total": int(sum(q["iters"] for q in seq))},
            "tol": tol,
            "timing": "wall clock around each call with device synchronisation; includes host tridiagonal solves"}
+    # Green function of the cluster's spin-up orbitals, G(i omega_n) on 64
+    # Matsubara points at beta_M = 50, and its gradient (bath energies and
+    # hybridisations included): the instances run concurrently on a pool of
+    # streams, against the one-instance calls one after another
+    orb = [(0, 0), (1, 0), (2, 0), (3, 0)]
+    z = 1j * (2 * np.arange(64) + 1) * np.pi / 50.0
+    blocks = 40
+    pkg.mcd_batch_band_lanczos_green(ctxs[:8], orb, blocks, 1.0, z, dtype=pkg.MCD_F32)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gb, dpb, dmb = pkg.mcd_batch_band_lanczos_green(ctxs, orb, blocks, 1.0, z, dtype=pkg.MCD_F32)
+    torch.cuda.synchronize()
+    t_bg = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Gs = [c.mcd_band_lanczos_green(orb, blocks, 1.0, z, dtype=pkg.MCD_F32)[0] for c in ctxs]
+    torch.cuda.synchronize()
+    t_sg = time.perf_counter() - t0
+    n_grad = 32
+    rng = np.random.default_rng(0)
+    gG = rng.normal(size=(n_grad, len(z), 4, 4)) + 1j * rng.normal(size=(n_grad, len(z), 4, 4))
+    t0 = time.perf_counter()
+    gb = pkg.mcd_batch_green_gradient(ctxs[:n_grad], orb, blocks, 1.0, z, gG, allow_not_converged=True)
+    t_bgr = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gs_ = [c.mcd_green_gradient(orb, blocks, 1.0, z, gG[i], allow_not_converged=True)
+           for i, c in enumerate(ctxs[:n_grad])]
+    t_sgr = time.perf_counter() - t0
+    out["green"] = {"orbitals": "cluster sites 0..3, spin up", "matsubara": "64 points, beta_M 50",
+                    "band_blocks": blocks, "w_t": 1.0, "vectors": "fp32 (fp64 ground state from the fp32 solve)",
+                    "excited_states_total": int(np.sum(dpb) + np.sum(dmb)),
+                    "batched_s": t_bg, "sequential_s": t_sg, "speedup": t_sg / t_bg,
+                    "bit_equal_to_single_calls": bool(all(np.array_equal(Gb[i], Gs[i]) for i in range(len(ctxs))))}
+    out["green_gradient"] = {"instances": n_grad, "batched_s": t_bgr, "sequential_s": t_sgr,
+                             "speedup": t_sgr / t_bgr,
+                             "bit_equal_to_single_calls": bool(all(np.array_equal(gb[1][i], gs_[i][1])
+                                                                   for i in range(n_grad)))}
     for c in ctxs:
         c.close()
     return out
@@ -491,6 +533,8 @@ def main():
     ap.add_argument("--no-rect24", action="store_true",
                     help="skip the 6x4 t-t' (24-site, 5e7-state) H*V measurements")
     ap.add_argument("--no-green", action="store_true", help="skip the band-Lanczos Green-function measurements")
+    ap.add_argument("--workload", default="square16", choices=["square16", "rect24"],
+                    help="lattice of the Lanczos steps (rect24: the 6x4 cluster, for profiling its kernels)")
     ap.add_argument("--green-c5-blocks", type=int, default=40,
                     help="band blocks per excited space of the 6x4 Green function")
     args = ap.parse_args()
@@ -510,7 +554,7 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
 
-    w = configs.square16_u8()
+    w = configs.square16_u8() if args.workload == "square16" else configs.rect24_u8()
     ctx = pkg.Context(local)
     ctx.mcd_set_hamiltonian(w.lat.t, w.eps, w.U, w.n_up, w.n_dn)
     if args.no_hv_cache:
@@ -578,8 +622,8 @@ def main():
     alg_bytes = n * (8 + 2 * 1 * 4)
     peak, peak_src = measured_peak()
     achieved = alg_bytes / ((tA + tB) * 1e-3) / 1e9
-    tb, ta = (None, None) if args.no_hv_cache else (traffic_for("hv_cached_pass_B_square16_fp32_L1"),
-                                                      traffic_for("hv_cached_pass_A_square16_fp32_L1"))
+    tb, ta = (None, None) if args.no_hv_cache or args.workload != "square16" else (
+        traffic_for("hv_cached_pass_B_square16_fp32_L1"), traffic_for("hv_cached_pass_A_square16_fp32_L1"))
     cinfo = ctx.mcd_hv_cache_info()
     rec_bytes = cinfo["bytes"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
