@@ -239,7 +239,9 @@ def workload_config(args, reference=False):
                 "n_dn": 11, "n_f": args.n_f, "mc_beta": 0.2, "mc_seed": 0, "lanczos_steps": args.iters, "ncols": 1,
                 "vectors": "fp32 (fp64 coefficients and reductions)",
                 "parallelism": f"replicas x{args.gpus}" if not reference else "cpu"}
-    return {"workload": "square4x4_tp-0.3_U8_Nup7_Ndn7_mcbasis1e7_lanczos200_fp32",
+    label = ("square4x4_tp-0.3_U8_Nup7_Ndn7_mcbasis1e7_lanczos200_fp32" if (args.n_f, args.iters) == (10_000_000, 200)
+             else f"square4x4_tp-0.3_U8_Nup7_Ndn7_mcbasis{args.n_f}_lanczos{args.iters}_fp32")
+    return {"workload": label,
             "lattice": "4x4 periodic square, R1=(4,0) R2=(0,4), t=1, t'=-0.3", "U": 8.0, "n_up": 7, "n_dn": 7,
             "n_f": args.n_f, "mc_beta": 0.2, "mc_seed": 0, "lanczos_steps": args.iters, "ncols": 1,
             "vectors": "fp32 (fp64 coefficients and reductions)",
