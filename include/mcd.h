@@ -119,6 +119,16 @@ typedef enum { MCD_F64 = 0, MCD_F32 = 1 } mcd_dtype;
                                    faster (default); 1 = pipelined tiles;
                                    2 = CTA per work item.  Same matrix, summed
                                    in another order (within rounding). */
+#define MCD_OPT_BATCH_SPLIT 11   /* batched calls (mcd_batch_*), read from
+                                   the first context: states per work unit of
+                                   the batched H*v are 1024 / value; 0 = the
+                                   first product of each batch size class
+                                   times value 1, 2 and 4 with 2, 4 and 8 CTAs
+                                   per SM and keeps the fastest (default).
+                                   Products are the same bit for bit for
+                                   every value; the Lanczos scalars <v, Hv>
+                                   are summed in another order (within
+                                   rounding). */
 #define MCD_OPT_HASH_ITEM 4     /* states per work item of the hash-lookup
                                    kernels: a power of two in [64, 4096]
                                    (default 1024).  Blocks of more states are

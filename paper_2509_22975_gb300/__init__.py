@@ -24,6 +24,7 @@ MCD_OPT_SAMPLER_DEVICE = 5
 MCD_OPT_HV_CACHE = 6
 MCD_OPT_APPLY_SYNC, MCD_OPT_WAIT_TEST, MCD_OPT_KRYLOV_STORE, MCD_OPT_HV_COLS = 7, 8, 9, 10
 HV_COLS_AUTO, HV_COLS_TILES, HV_COLS_ITEMS = 0, 1, 2
+MCD_OPT_BATCH_SPLIT = 11
 MCD_E_NOT_CONVERGED, MCD_E_TIMEOUT = -5, -7
 CACHE_AUTO, CACHE_OFF, CACHE_REQUIRED = 0, 1, 2
 SAMPLER_AUTO, SAMPLER_HOST, SAMPLER_DEVICE = 0, 1, 2

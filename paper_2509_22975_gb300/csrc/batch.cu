@@ -57,6 +57,7 @@ struct BInst {
 struct BItem {
   int inst;
   int item;              // work item of the instance's layout (kItem states)
+  int part;              // part of the item (its states split in `split` equal runs)
 };
 
 struct BArgs {
@@ -72,6 +73,7 @@ struct BArgs {
   double* partials;      // per work item <x, y> (pass A)
   int nw;                // bitmap words (2^nmax / 32)
   int xs_cap;            // elements of staged x
+  int split;             // parts per work item (the tile size is kItem / split states)
 };
 
 // Persistent H~v pass over all instances' work items, one column.
@@ -136,11 +138,20 @@ __global__ void __launch_bounds__(kBT) batch_hv_kernel(const BArgs a) {
     const int nb = s_nb, ns = s_nsites;
     const T* x = static_cast<const T*>(a.x) + int64_t(step) * a.xstride + ins.off;
     T* y = static_cast<T*>(a.y) + ins.off;
-    const int64_t k0 = int64_t(bi.item) * kItem;
-    const int64_t k1 = (k0 + kItem < L.n) ? k0 + kItem : L.n;
-    const uint32_t b0 = L.item_blk[bi.item];
-    uint32_t b1 = L.item_blk[bi.item + 1];
-    if (b1 == uint32_t(L.nblk) || L.blk_off[b1] == uint32_t(k1)) b1 -= 1;
+    // the states of this part of the work item, and the blocks they lie in
+    const int64_t ki0 = int64_t(bi.item) * kItem;
+    const int64_t ki1 = (ki0 + kItem < L.n) ? ki0 + kItem : L.n;
+    const int64_t chunk = (ki1 - ki0 + a.split - 1) / a.split;
+    const int64_t k0 = (ki0 + bi.part * chunk < ki1) ? ki0 + bi.part * chunk : ki1;
+    const int64_t k1 = (k0 + chunk < ki1) ? k0 + chunk : ki1;
+    if (k0 >= k1) {
+      if (DOT && threadIdx.x == 0) a.partials[ii] = 0.0;
+      continue;
+    }
+    uint32_t b0 = L.item_blk[bi.item];
+    while (int64_t(L.blk_off[b0 + 1]) <= k0) ++b0;
+    uint32_t b1 = b0;
+    while (int64_t(b1) + 1 < L.nblk && int64_t(L.blk_off[b1 + 1]) < k1) ++b1;
     double dot_acc = 0.0;
     for (uint32_t blk = b0; blk <= b1; ++blk) {
       const int bs = int(L.blk_off[blk]), be = int(L.blk_off[blk + 1]);
@@ -257,12 +268,14 @@ __global__ void __launch_bounds__(kBT) bstart_kernel(T* V, const int64_t* off, u
 }
 
 // dot[i][step] = sum of the instance's pass-A item partials, in item order
+// (split parts per work item: the instance's parts are contiguous)
 __global__ void bdot_kernel(const BInst* inst, int n_inst, const double* partials, const int* step, double* dot,
-                            int cap, const int* active) {
+                            int cap, const int* active, int split) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_inst || !active[i]) return;
   double s = 0.0;
-  for (int t = 0; t < inst[i].nitem[1]; ++t) s += partials[inst[i].item0[1] + t];
+  const int64_t t0 = int64_t(split) * inst[i].item0[1], t1 = t0 + int64_t(split) * inst[i].nitem[1];
+  for (int64_t t = t0; t < t1; ++t) s += partials[t];
   dot[int64_t(i) * cap + *step] = s;
 }
 
@@ -316,15 +329,27 @@ __global__ void __launch_bounds__(kBT) bnorm_kernel(const T* V, int64_t ntot, co
   }
 }
 
-// psi64 of every instance = sum_j coef[i][j] s_j (fp64)
-template <typename T>
-__global__ void bcombine_kernel(double* psi, const T* V, int64_t ntot, const int64_t* off, int n_inst,
+// psi64 of every instance = sum_j coef[i][j] s_j: fp64 for fp64 vectors,
+// double-float (df_fma, coefficients as (hi, lo) floats) for fp32 vectors
+__global__ void bcombine_kernel(double* psi, const double* V, int64_t ntot, const int64_t* off, int n_inst,
                                 const double* coef, const int* m, int cap) {
   for (int64_t k = int64_t(blockIdx.x) * kBT + threadIdx.x; k < ntot; k += int64_t(gridDim.x) * kBT) {
     const int i = inst_of(off, n_inst, k);
     double acc = 0.0;
-    for (int j = 0; j < m[i]; ++j) acc = fma(coef[int64_t(i) * cap + j], double(V[int64_t(j) * ntot + k]), acc);
+    for (int j = 0; j < m[i]; ++j) acc = fma(coef[int64_t(i) * cap + j], V[int64_t(j) * ntot + k], acc);
     psi[k] = acc;
+  }
+}
+__global__ void bcombine32_kernel(double* psi, const float* V, int64_t ntot, const int64_t* off, int n_inst,
+                                  const float2* coef, const int* m, int cap) {
+  for (int64_t k = int64_t(blockIdx.x) * kBT + threadIdx.x; k < ntot; k += int64_t(gridDim.x) * kBT) {
+    const int i = inst_of(off, n_inst, k);
+    float h = 0.f, l = 0.f;
+    for (int j = 0; j < m[i]; ++j) {
+      const float2 c = coef[int64_t(i) * cap + j];
+      df_fma(h, l, c.x, c.y, V[int64_t(j) * ntot + k]);
+    }
+    psi[k] = double(h) + double(l);
   }
 }
 
@@ -365,8 +390,14 @@ struct DevPtr {
 
 // grid sizes the autotuner tries (CTAs per SM) and its memory, per size class
 const int kGridCand[] = {2, 4, 8};
+const int kSplitCand[] = {1, 2, 4};   // parts per work item: tiles of kItem, kItem / 2, kItem / 4 states
+constexpr int kNSplit = 3;
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tuned;   // (log2 total, log2 n_inst) -> CTAs per SM
+struct Tuned {
+  int cps = 2;     // CTAs per SM
+  int split = 1;   // parts per work item
+};
+std::map<std::pair<int, int>, Tuned> g_tuned;   // (log2 total, log2 n_inst) -> grid and tile
 
 class Batch {
  public:
@@ -397,7 +428,7 @@ class Batch {
         const Layout& L = p ? c->idx.A : c->idx.B;
         inst[i].item0[p] = int(items[p].size());
         inst[i].nitem[p] = int(L.n_items);
-        for (int64_t t = 0; t < L.n_items; ++t) items[p].push_back(BItem{i, int(t)});
+        for (int64_t t = 0; t < L.n_items; ++t) items[p].push_back(BItem{i, int(t), 0});
       }
     }
     ntot_ = off_[n_];
@@ -408,17 +439,23 @@ class Batch {
     for (int i = 0; i < n_; ++i) inst[i].hp = hps_.as<HamParams>() + i;
     if (e == cudaSuccess) e = inst_.alloc(sizeof(BInst) * n_);
     if (e == cudaSuccess) e = cudaMemcpy(inst_.p, inst.data(), sizeof(BInst) * n_, cudaMemcpyHostToDevice);
-    for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
-      nitems_[p] = int(items[p].size());
-      e = items_[p].alloc(sizeof(BItem) * items[p].size());
-      if (e == cudaSuccess)
-        e = cudaMemcpy(items_[p].p, items[p].data(), sizeof(BItem) * items[p].size(), cudaMemcpyHostToDevice);
-    }
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p)
+      for (int si = 0; si < kNSplit && e == cudaSuccess; ++si) {
+        const int sp = kSplitCand[si];
+        std::vector<BItem> parts;
+        parts.reserve(items[p].size() * sp);
+        for (const BItem& b : items[p])
+          for (int q = 0; q < sp; ++q) parts.push_back(BItem{b.inst, b.item, q});
+        nitems_[p][si] = int(parts.size());
+        e = items_[p][si].alloc(sizeof(BItem) * parts.size());
+        if (e == cudaSuccess)
+          e = cudaMemcpy(items_[p][si].p, parts.data(), sizeof(BItem) * parts.size(), cudaMemcpyHostToDevice);
+      }
     if (e == cudaSuccess) e = offd_.alloc(sizeof(int64_t) * (n_ + 1));
     if (e == cudaSuccess) e = cudaMemcpy(offd_.p, off_.data(), sizeof(int64_t) * (n_ + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = counters_.alloc(sizeof(int) * 2 + sizeof(unsigned int) + sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(counters_.p, 0, sizeof(int) * 2 + sizeof(unsigned int) + sizeof(int));
-    if (e == cudaSuccess) e = partials_.alloc(sizeof(double) * std::max(nitems_[1], 1));
+    if (e == cudaSuccess) e = partials_.alloc(sizeof(double) * std::max(nitems_[1][kNSplit - 1], 1));
     if (e == cudaSuccess) e = active_.alloc(sizeof(int) * n_);
     if (e != cudaSuccess) return cuda_fail(c0_, e, "batch tables");
     std::vector<int> ones(n_, 1);
@@ -443,7 +480,10 @@ class Batch {
 
   // one H~v pair: x + step*xstride -> y over all instances (dot: fused <x, y>)
   template <typename T>
-  cudaError_t hv(const T* x, int64_t xstride, const int* stepp, T* y, bool dot, int ctas_per_sm) {
+  cudaError_t hv(const T* x, int64_t xstride, const int* stepp, T* y, bool dot, Tuned tc) {
+    const int ctas_per_sm = tc.cps;
+    int si = 0;
+    while (si + 1 < kNSplit && kSplitCand[si] != tc.split) ++si;
     BArgs a{};
     a.inst = inst_.as<BInst>();
     a.x = x;
@@ -454,6 +494,7 @@ class Batch {
     a.partials = partials_.as<double>();
     a.nw = nw_;
     a.xs_cap = xs_cap<T>();
+    a.split = kSplitCand[si];
     const size_t smem = smem_bytes<T>();
     static std::atomic<bool> configured{false};
     if (!configured) {
@@ -463,12 +504,12 @@ class Batch {
       configured = true;
     }
     for (int p = 0; p < 2; ++p) {
-      a.items = items_[p].as<BItem>();
-      a.n_items = nitems_[p];
+      a.items = items_[p][si].as<BItem>();
+      a.n_items = nitems_[p][si];
       a.counter = counter(p);
       cudaError_t e = cudaMemsetAsync(counter(p), 0, sizeof(int), s_);
       if (e != cudaSuccess) return e;
-      const int grid = std::max(1, std::min(nitems_[p], device_sms() * ctas_per_sm));
+      const int grid = std::max(1, std::min(nitems_[p][si], device_sms() * ctas_per_sm));
       if (p == 0)
         batch_hv_kernel<T, false, false><<<grid, kBT, smem, s_>>>(a);
       else if (dot)
@@ -482,13 +523,16 @@ class Batch {
     return cudaSuccess;
   }
 
-  // grid size for this batch: remembered per size class, else timed
+  // persistent grid size and work-unit (tile) size for this batch:
+  // remembered per size class, else timed over every candidate pair; the
+  // first context's MCD_OPT_BATCH_SPLIT (when set) fixes the tile
   template <typename T>
-  int tune(const T* x, T* y) {
+  Tuned tune(const T* x, T* y) {
     int lt = 0, li = 0;
     while ((int64_t(1) << lt) < ntot_) ++lt;
     while ((1 << li) < n_) ++li;
-    {
+    const int forced = c0_->batch_split;
+    if (!forced) {
       std::lock_guard<std::mutex> g(g_tune_mu);
       auto it = g_tuned.find({lt, li});
       if (it != g_tuned.end()) return it->second;
@@ -496,25 +540,31 @@ class Batch {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = kGridCand[0];
+    Tuned best;
     float best_ms = 1e30f;
-    for (int cand : kGridCand) {
-      hv<T>(x, 0, nullptr, y, false, cand);   // warm-up
-      cudaEventRecord(e0, s_);
-      for (int r = 0; r < 3; ++r) hv<T>(x, 0, nullptr, y, false, cand);
-      cudaEventRecord(e1, s_);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = cand;
+    for (int sp : kSplitCand) {
+      if (forced && sp != forced) continue;
+      for (int cand : kGridCand) {
+        const Tuned tc{cand, sp};
+        hv<T>(x, 0, nullptr, y, false, tc);   // warm-up
+        cudaEventRecord(e0, s_);
+        for (int r = 0; r < 3; ++r) hv<T>(x, 0, nullptr, y, false, tc);
+        cudaEventRecord(e1, s_);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = tc;
+        }
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    std::lock_guard<std::mutex> g(g_tune_mu);
-    g_tuned[{lt, li}] = best;
+    if (!forced) {
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      g_tuned[{lt, li}] = best;
+    }
     return best;
   }
 
@@ -522,7 +572,7 @@ class Batch {
   int apply(const T* x, T* y) {
     cudaError_t e = sync_from(c0_->stream);
     if (e != cudaSuccess) return cuda_fail(c0_, e, "batch apply");
-    const int cps = tune<T>(x, y);
+    const Tuned cps = tune<T>(x, y);
     e = hv<T>(x, 0, nullptr, y, false, cps);
     if (e == cudaSuccess) e = sync_to(c0_->stream);
     return e == cudaSuccess ? MCD_OK : cuda_fail(c0_, e, "batch apply");
@@ -555,9 +605,9 @@ class Batch {
   std::vector<int64_t> off_;
   int64_t ntot_ = 0;
   int nmax_ = 1, nw_ = 1;
-  int nitems_[2] = {0, 0};
+  int nitems_[2][kNSplit] = {};
   cudaStream_t s_ = nullptr;
-  DevPtr hps_, inst_, items_[2], offd_, counters_, partials_, active_;
+  DevPtr hps_, inst_, items_[2][kNSplit], offd_, counters_, partials_, active_;
   cudaGraphExec_t graph_exec_ = nullptr;
 };
 
@@ -581,7 +631,7 @@ int Batch::lanczos(int max_iter, double tol, uint64_t seed, double* E0, int* ite
   if (e == cudaSuccess) e = cudaMemsetAsync(scal.p, 0, sizeof(double) * 2 * size_t(cap) * n_, s_);
   if (e == cudaSuccess) e = cudaMemsetAsync(step(), 0, sizeof(int), s_);
   if (e != cudaSuccess) return cuda_fail(c0_, e, "batch Lanczos start");
-  const int cps = tune<T>(V.as<T>(), W.as<T>());
+  const Tuned cps = tune<T>(V.as<T>(), W.as<T>());
   const uint64_t key = bmix(bmix(seed + kGammaB) ^ 0x4C414E43ull);   // same stream as one instance
   bstart_kernel<T><<<n_, kBT, 0, s_>>>(V.as<T>(), offd_.as<int64_t>(), key, nrm2, cap);
   MCD_LAUNCHED(c0_);
@@ -591,7 +641,7 @@ int Batch::lanczos(int max_iter, double tol, uint64_t seed, double* E0, int* ite
     cudaError_t er = hv<T>(V.as<T>(), ntot_, step(), W.as<T>(), true, cps);
     if (er != cudaSuccess) return er;
     bdot_kernel<<<(n_ + 127) / 128, 128, 0, s_>>>(inst_.as<BInst>(), n_, partials_.as<double>(), step(), dot, cap,
-                                                 active_.as<int>());
+                                                 active_.as<int>(), cps.split);
     MCD_LAUNCHED(c0_);
     bupdate_kernel<T><<<egrid(ntot_), kBT, 0, s_>>>(V.as<T>(), W.as<T>(), ntot_, offd_.as<int64_t>(), n_, nrm2, dot,
                                                     cap, step(), active_.as<int>());
@@ -695,17 +745,25 @@ int Batch::lanczos(int max_iter, double tol, uint64_t seed, double* E0, int* ite
     std::vector<double> cf(size_t(cap) * n_, 0.0);
     for (int i = 0; i < n_; ++i)
       for (int j = 0; j < m_of[i]; ++j) cf[size_t(i) * cap + j] = evs[i][j] / std::sqrt(hn[size_t(i) * cap + j]);
+    std::vector<float2> cf32(fp32 ? cf.size() : 0);
+    for (size_t k = 0; k < cf32.size(); ++k) cf32[k] = split_coef(cf[k]);
     e = psi64.alloc(sizeof(double) * ntot_);
     if (e == cudaSuccess) e = hpsi.alloc(sizeof(double) * ntot_);
     if (e == cudaSuccess) e = coef.alloc(sizeof(double) * cf.size());
     if (e == cudaSuccess) e = mdev.alloc(sizeof(int) * n_);
     if (e == cudaSuccess) e = dots.alloc(sizeof(double) * 2 * n_);
     if (e == cudaSuccess) e = scale.alloc(sizeof(double) * n_);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(coef.p, cf.data(), sizeof(double) * cf.size(), cudaMemcpyHostToDevice, s_);
+    if (e == cudaSuccess)
+      e = fp32 ? cudaMemcpyAsync(coef.p, cf32.data(), sizeof(float2) * cf32.size(), cudaMemcpyHostToDevice, s_)
+               : cudaMemcpyAsync(coef.p, cf.data(), sizeof(double) * cf.size(), cudaMemcpyHostToDevice, s_);
     if (e == cudaSuccess) e = cudaMemcpyAsync(mdev.p, m_of.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, s_);
     if (e != cudaSuccess) return cuda_fail(c0_, e, "batch Ritz vectors");
-    bcombine_kernel<T><<<egrid(ntot_), kBT, 0, s_>>>(psi64.as<double>(), V.as<T>(), ntot_, offd_.as<int64_t>(), n_,
-                                                     coef.as<double>(), mdev.as<int>(), cap);
+    if (fp32)
+      bcombine32_kernel<<<egrid(ntot_), kBT, 0, s_>>>(psi64.as<double>(), reinterpret_cast<const float*>(V.p), ntot_,
+                                                      offd_.as<int64_t>(), n_, coef.as<float2>(), mdev.as<int>(), cap);
+    else
+      bcombine_kernel<<<egrid(ntot_), kBT, 0, s_>>>(psi64.as<double>(), reinterpret_cast<const double*>(V.p), ntot_,
+                                                    offd_.as<int64_t>(), n_, coef.as<double>(), mdev.as<int>(), cap);
     MCD_LAUNCHED(c0_);
     std::vector<int> ones(n_, 1);
     e = cudaMemcpyAsync(active_.p, ones.data(), sizeof(int) * n_, cudaMemcpyHostToDevice, s_);

@@ -137,6 +137,41 @@ struct Coef {
   T hi, lo;
 };
 
+// Double-float accumulation in fp32 arithmetic: (h, l) += (chi + clo) v, the
+// product split exactly by an FMA and added by Knuth's two-sum followed by a
+// fast renormalisation (Dekker), so (h + l) carries about 46 significant bits.
+// Every operation is an explicitly rounded intrinsic: no contraction, the same
+// bits wherever the step runs.  fp32 Ritz vectors are summed this way (GB300
+// runs fp64 arithmetic and fp32 -> fp64 conversions at a small fraction of the
+// fp32 rate, which made an fp64 sum of fp32 Krylov vectors ALU-bound).
+__device__ __forceinline__ void df_fma(float& h, float& l, float chi, float clo, float v) {
+  const float ph = __fmul_rn(chi, v);
+  float pl = __fmaf_rn(chi, v, -ph);
+  pl = __fmaf_rn(clo, v, pl);
+  const float s = __fadd_rn(h, ph);
+  const float bb = __fsub_rn(s, h);
+  float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+  e = __fadd_rn(e, __fadd_rn(l, pl));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// (h, l) += x in double-float (two-sum, then the fast renormalisation)
+__device__ __forceinline__ void df_add(float& h, float& l, float x) {
+  const float s = __fadd_rn(h, x);
+  const float bb = __fsub_rn(s, h);
+  float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  e = __fadd_rn(e, l);
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// fp64 coefficient c as (hi, lo) floats: hi = fl32(c), lo = fl32(c - hi)
+__host__ __device__ __forceinline__ float2 split_coef(double c) {
+  const float hi = float(c);
+  return make_float2(hi, float(c - double(hi)));
+}
+
 template <typename T>
 __device__ __forceinline__ Coef<T> bond_coef(const float* thi, const float* tlo, const double* t64, int b,
                                              int sign);

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <vector>
 
+#include "hv_common.cuh"
 #include "mcd_internal.h"
 
 namespace mcd {
@@ -102,14 +103,31 @@ __device__ __forceinline__ void st(double* p, const double* v) {
   *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
 }
 
-// sum of squares of W stored values: fp32 partial then one fp64 add
+// sum of squares of W stored values (in T)
 template <typename T, int W>
-__device__ __forceinline__ double sumsq(const T* v) {
+__device__ __forceinline__ T sumsq(const T* v) {
   T s = T(0);
 #pragma unroll
   for (int i = 0; i < W; ++i) s = v[i] * v[i] + s;
-  return double(s);
+  return s;
 }
+
+// a thread's running sum of such partials: fp64 for fp64 vectors, double-float
+// (df_add) for fp32 vectors, so that no fp64 arithmetic runs per element
+template <typename T>
+struct RunSum;
+template <>
+struct RunSum<float> {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void add(float x) { df_add(h, l, x); }
+  __device__ __forceinline__ double value() const { return double(h) + double(l); }
+};
+template <>
+struct RunSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
 
 // s_0[k] = uniform[-1, 1) from SplitMix64(key ^ k) ; nrm2[0] = |s_0|^2
 template <typename T>
@@ -149,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const T* __restrict__ 
   const T al = c_al, be = c_be, ga = c_ga;
   const bool use_prev = s_use_prev;
   constexpr int W = V4<T>::W;
-  double acc = 0.0;
+  RunSum<T> acc;
   const int64_t nv = n / W;
   for (int64_t q = int64_t(blockIdx.x) * kThreads + threadIdx.x; q < nv; q += int64_t(gridDim.x) * kThreads) {
     T a[W], b[W], c[W], o[W];
@@ -159,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const T* __restrict__ 
 #pragma unroll
     for (int i = 0; i < W; ++i) o[i] = use_prev ? (al * a[i] + be * b[i] + ga * c[i]) : (al * a[i] + be * b[i]);
     st(out + q * W, o);
-    acc += sumsq<T, W>(o);
+    acc.add(sumsq<T, W>(o));
   }
   // tail
   if (blockIdx.x == 0) {
@@ -167,10 +185,10 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const T* __restrict__ 
       T o = al * w[k] + be * s[k];
       if (use_prev) o += ga * s_prev[k];
       out[k] = o;
-      acc += double(o) * double(o);
+      acc.add(o * o);
     }
   }
-  grid_sum(acc, partials, ticket, const_cast<double*>(scal) + sl.nrm2(step + 1));
+  grid_sum(acc.value(), partials, ticket, const_cast<double*>(scal) + sl.nrm2(step + 1));
 }
 
 // psi += coef * s
@@ -181,21 +199,85 @@ __global__ void axpy_kernel(T* psi, const T* s, int64_t n, double coef) {
     psi[k] += c * s[k];
 }
 
-// psi[k] = sum_{j < m} coef[j] V[j][k] in fp64 (V: m stored vectors, stride ld)
-template <typename T>
-__global__ void combine_kernel(double* psi, const T* V, int64_t n, int64_t ld, int m, const double* coef) {
+// psi[k] = sum_{j < m} coef[j] V[j][k] in fp64 (V: m stored fp64 vectors, stride ld)
+__global__ void combine_kernel(double* psi, const double* V, int64_t n, int64_t ld, int m, const double* coef) {
   for (int64_t k = int64_t(blockIdx.x) * kThreads + threadIdx.x; k < n; k += int64_t(gridDim.x) * kThreads) {
     double acc = 0.0;
-    for (int j = 0; j < m; ++j) acc = fma(__ldg(coef + j), double(V[int64_t(j) * ld + k]), acc);
+    for (int j = 0; j < m; ++j) acc = fma(__ldg(coef + j), V[int64_t(j) * ld + k], acc);
     psi[k] = acc;
   }
 }
 
-// psi64 += coef * double(s)
-template <typename T>
-__global__ void axpy64_kernel(double* psi, const T* s, int64_t n, double coef) {
+// The same sum over fp32 vectors in double-float (df_fma, coefficients split
+// as (hi, lo) floats), written out as double(h) + double(l): four positions
+// per thread (16-byte loads; ld is a multiple of 4 and V 16-byte aligned),
+// four vectors' loads issued before their arithmetic; the last n % 4
+// positions one by one.
+__global__ void __launch_bounds__(kThreads) combine32_kernel(double* psi, const float* __restrict__ V, int64_t n,
+                                                             int64_t ld, int m, const float2* __restrict__ coef) {
+  const int64_t nv = n / 4;
+  for (int64_t q = int64_t(blockIdx.x) * kThreads + threadIdx.x; q < nv; q += int64_t(gridDim.x) * kThreads) {
+    float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+    const float* vq = V + 4 * q;
+    int j = 0;
+    for (; j + 4 <= m; j += 4) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldcs(reinterpret_cast<const float4*>(vq + int64_t(j + u) * ld));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 c = __ldg(coef + j + u);
+        df_fma(h[0], l[0], c.x, c.y, v[u].x);
+        df_fma(h[1], l[1], c.x, c.y, v[u].y);
+        df_fma(h[2], l[2], c.x, c.y, v[u].z);
+        df_fma(h[3], l[3], c.x, c.y, v[u].w);
+      }
+    }
+    for (; j < m; ++j) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(vq + int64_t(j) * ld));
+      const float2 c = __ldg(coef + j);
+      df_fma(h[0], l[0], c.x, c.y, v.x);
+      df_fma(h[1], l[1], c.x, c.y, v.y);
+      df_fma(h[2], l[2], c.x, c.y, v.z);
+      df_fma(h[3], l[3], c.x, c.y, v.w);
+    }
+    double2* out = reinterpret_cast<double2*>(psi + 4 * q);
+    out[0] = make_double2(double(h[0]) + double(l[0]), double(h[1]) + double(l[1]));
+    out[1] = make_double2(double(h[2]) + double(l[2]), double(h[3]) + double(l[3]));
+  }
+  if (blockIdx.x == 0)
+    for (int64_t k = nv * 4 + threadIdx.x; k < n; k += kThreads) {
+      float h = 0.f, l = 0.f;
+      for (int j = 0; j < m; ++j) {
+        const float2 c = __ldg(coef + j);
+        df_fma(h, l, c.x, c.y, V[int64_t(j) * ld + k]);
+      }
+      psi[k] = double(h) + double(l);
+    }
+}
+
+// psi64 += coef * s (fp64 vectors)
+__global__ void axpy64_kernel(double* psi, const double* s, int64_t n, double coef) {
   for (int64_t k = int64_t(blockIdx.x) * kThreads + threadIdx.x; k < n; k += int64_t(gridDim.x) * kThreads)
-    psi[k] = fma(coef, double(s[k]), psi[k]);
+    psi[k] = fma(coef, s[k], psi[k]);
+}
+
+// one term of combine32_kernel's sum when the vectors are regenerated: the
+// double-float state (h, l) of each position is kept in psi's own 8 bytes
+__global__ void axpy_df_kernel(float2* acc, const float* s, int64_t n, float chi, float clo) {
+  for (int64_t k = int64_t(blockIdx.x) * kThreads + threadIdx.x; k < n; k += int64_t(gridDim.x) * kThreads) {
+    float2 a = acc[k];
+    df_fma(a.x, a.y, chi, clo, s[k]);
+    acc[k] = a;
+  }
+}
+
+// psi[k] = double(h) + double(l) in place of the state (h, l) at the same 8 bytes
+__global__ void finish_df_kernel(double* psi, int64_t n) {
+  for (int64_t k = int64_t(blockIdx.x) * kThreads + threadIdx.x; k < n; k += int64_t(gridDim.x) * kThreads) {
+    const float2 a = reinterpret_cast<const float2*>(psi)[k];
+    psi[k] = double(a.x) + double(a.y);
+  }
 }
 
 // out[k] = T(v[k] * f)
@@ -384,25 +466,40 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
   // for the fp32 form (whose E0 is then the fp64 Rayleigh quotient of it)
   std::vector<double> coef(m);
   for (int k = 0; k < m; ++k) coef[k] = ev[k] / std::sqrt(nrm2[k]);
+  // (fp32 vectors: double-float sum, the same steps whether the vectors are
+  // stored or regenerated, so both give the same bits)
   double* p64 = fp32 ? w.psi64 : reinterpret_cast<double*>(psi);
+  std::vector<float2> coef32(fp32 ? m : 0);
+  for (size_t k = 0; k < coef32.size(); ++k) coef32[k] = split_coef(coef[k]);
   if (w.stored) {
-    e = cudaMemcpyAsync(w.coef, coef.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s);
+    e = fp32 ? cudaMemcpyAsync(w.coef, coef32.data(), sizeof(float2) * m, cudaMemcpyHostToDevice, s)
+             : cudaMemcpyAsync(w.coef, coef.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "Ritz coefficients");
-    if (fp32 || sizeof(T) == 8) {
-      combine_kernel<T><<<vg, kThreads, 0, s>>>(p64, V, n, w.ld, m, w.coef);
-      MCD_LAUNCHED(c);
-    }
+    if (fp32)
+      combine32_kernel<<<vg, kThreads, 0, s>>>(p64, reinterpret_cast<const float*>(V), n, w.ld, m,
+                                               reinterpret_cast<const float2*>(w.coef));
+    else
+      combine_kernel<<<vg, kThreads, 0, s>>>(p64, reinterpret_cast<const double*>(V), n, w.ld, m, w.coef);
+    MCD_LAUNCHED(c);
   } else {
     e = cudaMemsetAsync(p64, 0, sizeof(double) * n, s);
     if (e == cudaSuccess) e = fresh_start();
     if (e != cudaSuccess) return cuda_fail(c, e, "Ritz vector");
     for (int k = 0; k < m; ++k) {
-      axpy64_kernel<T><<<vg, kThreads, 0, s>>>(p64, vec(k), n, coef[k]);
+      if (fp32)
+        axpy_df_kernel<<<vg, kThreads, 0, s>>>(reinterpret_cast<float2*>(p64),
+                                               reinterpret_cast<const float*>(vec(k)), n, coef32[k].x, coef32[k].y);
+      else
+        axpy64_kernel<<<vg, kThreads, 0, s>>>(p64, reinterpret_cast<const double*>(vec(k)), n, coef[k]);
       MCD_LAUNCHED(c);
       if (k + 1 < m) {
         int st = step(k);
         if (st != MCD_OK) return st;
       }
+    }
+    if (fp32) {
+      finish_df_kernel<<<vg, kThreads, 0, s>>>(p64, n);
+      MCD_LAUNCHED(c);
     }
   }
   // |psi|^2, <psi, H psi>, |H psi - E psi|^2 in fp64

@@ -273,6 +273,11 @@ int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
       if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "HV_COLS must be 0, 1 or 2");
       c->hv_cols = int(value);
       return MCD_OK;
+    case MCD_OPT_BATCH_SPLIT:
+      if (value != 0 && value != 1 && value != 2 && value != 4)
+        return fail(c, MCD_E_INVALID, "BATCH_SPLIT must be 0, 1, 2 or 4");
+      c->batch_split = int(value);
+      return MCD_OK;
     case MCD_OPT_APPLY_SYNC:
       if (value < 0 || value > 1) return fail(c, MCD_E_INVALID, "APPLY_SYNC must be 0 or 1");
       c->apply_sync = int(value);

@@ -46,14 +46,21 @@ def concat(parts, dtype):
     return torch.cat([torch.as_tensor(p, dtype=dtype) for p in parts]).to(DEV)
 
 
+@pytest.mark.parametrize("split", [0, 1, 2, 4])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_batch_apply_equals_single_and_oracle(batch12, dtype):
+def test_batch_apply_equals_single_and_oracle(batch12, dtype, split):
+    # every work-unit size (timed pick, or 1024, 512 and 256 states per
+    # unit) gives the same product bit for bit
     ms, ctxs = batch12
     sizes = [c.mcd_basis_info(nnz=False)["n_states"] for c in ctxs]
     g = torch.Generator(device=DEV).manual_seed(3)
     x = torch.randn(sum(sizes), dtype=dtype, device=DEV, generator=g)
     y = torch.full_like(x, float("nan"))
-    pkg.mcd_batch_apply(ctxs, x, y)
+    ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_SPLIT, split)
+    try:
+        pkg.mcd_batch_apply(ctxs, x, y)
+    finally:
+        ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_SPLIT, 0)
     torch.cuda.synchronize()
     off = np.concatenate([[0], np.cumsum(sizes)])
     u = U64 if dtype == torch.float64 else U32
@@ -107,6 +114,20 @@ def test_batch_lanczos_fp32_and_ritz_vectors(batch12):
         v = p.cpu().numpy()
         res = P.sparse() @ v - r32["E0"][i] * v
         assert np.linalg.norm(res) < 1e-3
+
+
+@pytest.mark.parametrize("split", [1, 4])
+def test_batch_lanczos_every_work_unit_size(batch12, split):
+    # the fused <v, Hv> partials are summed per work unit: another unit size
+    # sums them in another order, so E0 agrees within rounding
+    ms, ctxs = batch12
+    ref = pkg.mcd_batch_lanczos_ground(ctxs, 400, 1e-12, 0, pkg.MCD_F64)
+    ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_SPLIT, split)
+    try:
+        r = pkg.mcd_batch_lanczos_ground(ctxs, 400, 1e-12, 0, pkg.MCD_F64)
+    finally:
+        ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_SPLIT, 0)
+    assert np.max(np.abs(r["E0"] - ref["E0"]) / np.abs(ref["E0"])) <= 1e-10
 
 
 def test_batch_is_deterministic(batch12):
