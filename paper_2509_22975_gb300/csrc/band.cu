@@ -23,6 +23,9 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+
+#include "hv_common.cuh"
 #include "mcd_internal.h"
 
 namespace mcd {
@@ -113,57 +116,167 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ X,
   }
 }
 
-// fp32 vectors: the same partial sums without fp64 multiplies (GB300's fp64
-// rate is a small fraction of its fp32 rate).  Each product is split exactly
-// into p + e (e = fma(x, y, -p)) and summed into a double-float (hi, lo) over
-// one tile of rows; the tile's sum hi + lo is added to the fp64 partial.
-__global__ void __launch_bounds__(kThreads) gram32_kernel(const float* __restrict__ X, int pa,
-                                                          const float* __restrict__ Y, int pb, int ld, int64_t n,
-                                                          double* partials) {
-  constexpr int kRows = 32;
-  __shared__ float xs[kRows][kMaxOrb];
-  __shared__ float ys[kRows][kMaxOrb];
-  const int npair = pa * pb;
-  constexpr int kPer = kMaxOrb * kMaxOrb / kThreads;
-  double acc[kPer];
+// fp32 vectors: the same partial sums on the tensor cores.  Every value is
+// split exactly into three bf16 pieces, x = x0 + x1 + x2 (round to nearest
+// leaves at most 16 and then 8 significant bits, so the third piece is the
+// exact remainder); the products x_i y_j with i + j <= 2 are exact in fp32
+// and the warp-level MMA (m16n8k16, bf16 in, fp32 accumulate) sums them over
+// one chunk of rows; each chunk's fp32 sums are then added to a double-float
+// (hi, lo) per Gram entry, whose hi + lo goes into the CTA's fp64 partial.
+// The dropped products are below 2^-24 of |x y| and the fp32 rounding stays
+// inside each chunk, so an entry carries about 2^-24 sqrt(6 n) rms(x y) of
+// error: ~1e-11 of |x| |y| on 5e7 rows.
+//
+// CTA: 8 warps, kGR rows per iteration.  The slices are kept transposed in
+// shared memory (orbital-major, two rows per 32-bit word, kGW words per
+// orbital, kGW = 4 mod 32, so fragment loads hit 32 distinct banks).  The
+// output (pa x pb, padded to 16 x 8 tiles) is cut into warp blocks of 2 x 2
+// tiles; with fewer than 8 blocks, the warps of one block split the chunk's
+// 16-row steps between them.
+constexpr int kGR = 128;                 // rows per CTA iteration
+constexpr int kGW = kGR / 2 + 4;         // 32-bit words per orbital and slice
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// bf16 bits of round-to-nearest(v), and v minus that value (exact)
+__device__ __forceinline__ uint32_t bf16_split(float& v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  v = __fsub_rn(v, __bfloat162float(h));
+  return uint32_t(__bfloat16_as_ushort(h));
+}
+
+// the chunk's rows [r0, r0 + kGR) of columns [0, p) of M as three transposed
+// bf16 slices: word (s, c, kp) holds rows 2 kp (low half) and 2 kp + 1
+__device__ __forceinline__ void gram_stage(const float* __restrict__ M, int p, int ld, int64_t n, int64_t r0,
+                                           uint32_t* sl, int cpad) {
+  for (int e = threadIdx.x; e < (kGR / 2) * p; e += kThreads) {
+    const int kp = e / p, c = e - kp * p;
+    const int64_t ra = r0 + 2 * kp, rb = ra + 1;
+    float va = ra < n ? __ldg(M + ra * ld + c) : 0.f;
+    float vb = rb < n ? __ldg(M + rb * ld + c) : 0.f;
 #pragma unroll
-  for (int u = 0; u < kPer; ++u) acc[u] = 0.0;
-  for (int64_t r0 = int64_t(blockIdx.x) * kRows; r0 < n; r0 += int64_t(gridDim.x) * kRows) {
-    for (int e = threadIdx.x; e < kRows * pa; e += kThreads) {
-      const int rr = e / pa, cc = e - rr * pa;
-      const int64_t r = r0 + rr;
-      xs[rr][cc] = r < n ? X[r * ld + cc] : 0.f;
+    for (int s = 0; s < 3; ++s) {
+      const uint32_t lo = bf16_split(va), hi = bf16_split(vb);
+      sl[(s * cpad + c) * kGW + kp] = lo | (hi << 16);
     }
-    for (int e = threadIdx.x; e < kRows * pb; e += kThreads) {
-      const int rr = e / pb, cc = e - rr * pb;
-      const int64_t r = r0 + rr;
-      ys[rr][cc] = r < n ? Y[r * ld + cc] : 0.f;
-    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) gram_tc_kernel(const float* __restrict__ X, int pa,
+                                                           const float* __restrict__ Y, int pb, int ld, int64_t n,
+                                                           double* partials) {
+  extern __shared__ __align__(16) uint32_t s_gram[];
+  const int Mt = (pa + 15) / 16, Nt = (pb + 7) / 8;
+  const int Mp = Mt * 16, Np = Nt * 8;
+  uint32_t* xs = s_gram;                       // [3][Mp][kGW]
+  uint32_t* ys = s_gram + 3 * Mp * kGW;        // [3][Np][kGW]
+  for (int i = threadIdx.x; i < 3 * (Mp + Np) * kGW; i += kThreads) s_gram[i] = 0u;   // padding stays zero
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int nmb = (Mt + 1) / 2, nnb = (Nt + 1) / 2, nblk = nmb * nnb;
+  const int kparts = nblk >= 5 ? 1 : (nblk >= 3 ? 2 : (nblk == 2 ? 4 : 8));
+  const bool busy = warp < nblk * kparts;
+  const int blk = warp % nblk, kp = warp / nblk;
+  const int mt0 = (blk / nnb) * 2, nt0 = (blk % nnb) * 2;
+  constexpr int kSteps = kGR / 16;
+  const int ksteps = kSteps / kparts, ks0 = kp * ksteps;
+  float acc[2][2][4], dh[2][2][4], dl[2][2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = dh[i][j][q] = dl[i][j][q] = 0.f;
+  for (int64_t r0 = int64_t(blockIdx.x) * kGR; r0 < n; r0 += int64_t(gridDim.x) * kGR) {
+    __syncthreads();   // the previous chunk's slices are consumed
+    gram_stage(X, pa, ld, n, r0, xs, Mp);
+    gram_stage(Y, pb, ld, n, r0, ys, Np);
     __syncthreads();
+    if (!busy) continue;
+    for (int ks = ks0; ks < ks0 + ksteps; ++ks) {
+      const int kw = ks * 8 + t;   // word of rows 16 ks + 2t, 2t + 1
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      const int pr = threadIdx.x + u * kThreads;
-      if (pr < npair) {
-        const int ia = pr / pb, ib = pr - (pr / pb) * pb;
-        float hi = 0.f, lo = 0.f;
-        for (int rr = 0; rr < kRows; ++rr) {
-          const float x = xs[rr][ia], y = ys[rr][ib];
-          const float p = x * y;
-          const float e = fmaf(x, y, -p);
-          const float sum = hi + p, bb = sum - hi;
-          lo += ((hi - (sum - bb)) + (p - bb)) + e;
-          hi = sum;
+      for (int i = 0; i < 3; ++i) {
+        uint32_t a[2][4];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+          const uint32_t* base = xs + (i * Mp + (mt0 + mi) * 16 + g) * kGW + kw;
+          const bool ok = mt0 + mi < Mt;
+          a[mi][0] = ok ? base[0] : 0u;
+          a[mi][1] = ok ? base[8 * kGW] : 0u;
+          a[mi][2] = ok ? base[4] : 0u;
+          a[mi][3] = ok ? base[8 * kGW + 4] : 0u;
         }
-        acc[u] += double(hi) + double(lo);
+#pragma unroll
+        for (int j = 0; i + j < 3; ++j) {
+          uint32_t b[2][2];
+#pragma unroll
+          for (int ni = 0; ni < 2; ++ni) {
+            const uint32_t* base = ys + (j * Np + (nt0 + ni) * 8 + g) * kGW + kw;
+            const bool ok = nt0 + ni < Nt;
+            b[ni][0] = ok ? base[0] : 0u;
+            b[ni][1] = ok ? base[4] : 0u;
+          }
+#pragma unroll
+          for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < 2; ++ni)
+              if (mt0 + mi < Mt && nt0 + ni < Nt) mma_bf16_16816(acc[mi][ni], a[mi], b[ni]);
+        }
       }
     }
-    __syncthreads();
-  }
+    // the chunk's sums into the double-float accumulators
 #pragma unroll
-  for (int u = 0; u < kPer; ++u) {
-    const int pr = threadIdx.x + u * kThreads;
-    if (pr < npair) partials[int64_t(blockIdx.x) * npair + pr] = acc[u];
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          df_add(dh[mi][ni][q], dl[mi][ni][q], acc[mi][ni][q]);
+          acc[mi][ni][q] = 0.f;
+        }
   }
+  // CTA partial: the warps' entries (fp64) by split, summed in split order
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(s_gram);   // [kparts][Mp][Np]
+  if (busy) {
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+        if (mt0 + mi < Mt && nt0 + ni < Nt) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int m = (mt0 + mi) * 16 + g + (q >> 1) * 8;
+            const int nn = (nt0 + ni) * 8 + 2 * t + (q & 1);
+            red[(int64_t(kp) * Mp + m) * Np + nn] = double(dh[mi][ni][q]) + double(dl[mi][ni][q]);
+          }
+        }
+  }
+  __syncthreads();
+  const int npair = pa * pb;
+  for (int pr = threadIdx.x; pr < npair; pr += kThreads) {
+    const int ia = pr / pb, ib = pr - ia * pb;
+    double v = 0.0;
+    for (int k = 0; k < kparts; ++k) v += red[(int64_t(k) * Mp + ia) * Np + ib];
+    partials[int64_t(blockIdx.x) * npair + pr] = v;
+  }
+}
+
+// shared memory of gram_tc_kernel for pa x pb
+size_t gram_tc_smem(int pa, int pb) {
+  const int Mp = (pa + 15) / 16 * 16, Np = (pb + 7) / 8 * 8;
+  const int nblk = ((Mp / 16 + 1) / 2) * ((Np / 8 + 1) / 2);
+  const int kparts = nblk >= 5 ? 1 : (nblk >= 3 ? 2 : (nblk == 2 ? 4 : 8));
+  const size_t slices = size_t(3) * (Mp + Np) * kGW * 4;
+  const size_t red = size_t(kparts) * Mp * Np * 8;
+  return std::max(slices, red);
 }
 
 __global__ void reduce_partials_kernel(const double* partials, int nparts, int npair, double* out) {
@@ -198,6 +311,155 @@ __global__ void block_combine32_kernel(const float* W, float* out, int pw, float
     for (int i = 0; i < p1; ++i) df_add(hi, lo, X1[r * ld + i], __ldg(CH1 + i * pw + j), __ldg(CL1 + i * pw + j));
     for (int i = 0; i < p2; ++i) df_add(hi, lo, X2[r * ld + i], __ldg(CH2 + i * pw + j), __ldg(CL2 + i * pw + j));
     out[r * ld + j] = hi + lo;
+  }
+}
+
+// fp32 vectors, K = p1 + p2 <= 64 and pw <= 32: the same combination on the
+// tensor cores with exact integer sums.  Each row r of [X1 X2] is scaled by a
+// power of two 2^(8 - e_r) (its largest |x| < 2^e_r) and cut into four
+// round-to-nearest slices of at most 8 bits (|q_0| <= 256, |q_i| <= 128: bf16
+// integers), the coefficients likewise per column j (scale 2^(8 - f_j), cut on
+// the host from the fp64 values).  The MMA sums the slice products of one
+// level l = i + j (i, j < 4, l <= 3) into an fp32 accumulator of its own:
+// integers below 4 * 64 * 2^15 < 2^24, so every sum is exact.  The four levels
+// are then combined in double-float, scaled by 2^(e_r + f_j - 16), beta W is
+// added exactly and the result rounded once to fp32.  What is lost are the
+// slices' remainders, below 2^-33 of the row's and the column's largest
+// entries: ~1e-9 of sum |x c|.
+constexpr int kCK = 64;          // largest K of the tensor-core combination
+constexpr int kCN = 32;          // largest pw
+constexpr int kCW = kCK / 2 + 4; // 32-bit words per coefficient column and slice (= 4 mod 32)
+
+// this thread's values of rows r0 + g, r0 + g + 8 and columns 16 ks + 2t + {0, 1, 8, 9} of [X1 X2]
+template <int KS>
+__device__ __forceinline__ void combine_tc_load(const float* __restrict__ X1, int p1, const float* __restrict__ X2,
+                                                int K, int ld, int64_t n, int64_t r0, int g, int t,
+                                                float (&v)[2][KS][4]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t r = r0 + g + 8 * h;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = 16 * ks + 2 * t + (q & 1) + (q >> 1) * 8;
+        float x = 0.f;
+        if (r < n && k < K) x = k < p1 ? __ldg(X1 + r * ld + k) : __ldg(X2 + r * ld + (k - p1));
+        v[h][ks][q] = x;
+      }
+  }
+}
+
+template <int KS, int NT>
+__global__ void __launch_bounds__(kThreads, 1) block_combine_tc_kernel(const float* W, float* out, int pw, float bh,
+                                                                       float bl, const float* __restrict__ X1, int p1,
+                                                                       const float* __restrict__ X2, int p2,
+                                                                       const uint32_t* __restrict__ cslices,
+                                                                       const int* __restrict__ fexp, int ld,
+                                                                       int64_t n) {
+  __shared__ uint32_t s_c[4 * NT * 8 * kCW];   // [slice][n][word of k pairs]
+  __shared__ int s_f[NT * 8];
+  for (int i = threadIdx.x; i < 4 * NT * 8 * kCW; i += kThreads) s_c[i] = cslices[i];
+  for (int i = threadIdx.x; i < NT * 8; i += kThreads) s_f[i] = fexp[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int K = p1 + p2;
+  const int64_t ntile = (n + 15) / 16;
+  const int64_t stride = int64_t(gridDim.x) * (kThreads / 32);
+  int64_t tile = int64_t(blockIdx.x) * (kThreads / 32) + warp;
+  float v[2][KS][4];
+  if (tile < ntile) combine_tc_load<KS>(X1, p1, X2, K, ld, n, tile * 16, g, t, v);
+  for (; tile < ntile; tile += stride) {
+    const int64_t r0 = tile * 16;
+    // row scales: the largest |x| of the row (over the quad's four threads)
+    int er[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float mx = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mx = fmaxf(mx, fabsf(v[h][ks][q]));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      // mx in [2^(e-1), 2^e); rows below 2^-119 are taken as zero
+      const int e = int((__float_as_uint(mx) >> 23) & 0xFFu) - 126;
+      const bool live = mx >= 0x1p-119f;
+      er[h] = live ? e : 0;
+      const float sc = live ? __uint_as_float(uint32_t(127 + 8 - e) << 23) : 0.f;
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[h][ks][q] *= sc;   // exact: |v| < 256
+    }
+    // slice by slice (q = rint(v), v <- 256 (v - q), both exact): the MMA sums
+    // the products with the coefficient slices j <= 3 - i into the level
+    // i + j accumulator, exact fp32 integers
+    float acc[4][NT][4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[l][nt][q] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uint32_t a[KS][4];
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        uint32_t qb[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float qi = rintf(v[h][ks][q]);
+            v[h][ks][q] = __fmul_rn(__fsub_rn(v[h][ks][q], qi), 256.f);
+            qb[h][q] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(qi)));
+          }
+        a[ks][0] = qb[0][0] | (qb[0][1] << 16);
+        a[ks][1] = qb[1][0] | (qb[1][1] << 16);
+        a[ks][2] = qb[0][2] | (qb[0][3] << 16);
+        a[ks][3] = qb[1][2] | (qb[1][3] << 16);
+      }
+#pragma unroll
+      for (int j = 0; i + j < 4; ++j)
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            const uint32_t* bp = s_c + (j * NT * 8 + nt * 8 + g) * kCW + ks * 8 + t;
+            const uint32_t b[2] = {bp[0], bp[4]};
+            mma_bf16_16816(acc[i + j][nt], a[ks], b);
+          }
+    }
+    // the next tile's values load while this one's results are formed
+    if (tile + stride < ntile) combine_tc_load<KS>(X1, p1, X2, K, ld, n, (tile + stride) * 16, g, t, v);
+    // the levels in double-float, weight 2^(-8 l)
+    float oh[NT][4], ol[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        oh[nt][q] = acc[0][nt][q];
+        ol[nt][q] = 0.f;
+        df_add(oh[nt][q], ol[nt][q], __fmul_rn(acc[1][nt][q], 0x1p-8f));
+        df_add(oh[nt][q], ol[nt][q], __fmul_rn(acc[2][nt][q], 0x1p-16f));
+        df_add(oh[nt][q], ol[nt][q], __fmul_rn(acc[3][nt][q], 0x1p-24f));
+      }
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int h = q >> 1;
+        const int64_t r = r0 + g + 8 * h;
+        const int j = nt * 8 + 2 * t + (q & 1);
+        if (r >= n || j >= pw) continue;
+        const int sh = er[h] + s_f[j] - 16;
+        float hi = ldexpf(oh[nt][q], sh), lo = ldexpf(ol[nt][q], sh);
+        if (bh != 0.f || bl != 0.f) df_add(hi, lo, W[r * ld + j], bh, bl);
+        out[r * ld + j] = hi + lo;
+      }
   }
 }
 
@@ -436,9 +698,15 @@ class BandLanczos {
   // host G = X[:, :pa]^T Y[:, :pb]
   int gram(const T* X, int pa, const T* Y, int pb, std::vector<double>& G) {
     cudaStream_t s = c_->stream;
-    if constexpr (sizeof(T) == 4)
-      gram32_kernel<<<nparts_, kThreads, 0, s>>>(X, pa, Y, pb, L_, n_, part_);
-    else
+    if constexpr (sizeof(T) == 4) {
+      const size_t smem = gram_tc_smem(pa, pb);
+      if (smem > 48 * 1024) {
+        const cudaError_t ea =
+            cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (ea != cudaSuccess) return cuda_fail(c_, ea, "Gram kernel shared memory");
+      }
+      gram_tc_kernel<<<nparts_, kThreads, smem, s>>>(X, pa, Y, pb, L_, n_, part_);
+    } else
       gram_kernel<T><<<nparts_, kThreads, 0, s>>>(X, pa, Y, pb, L_, n_, part_);
     MCD_LAUNCHED(c_);
     reduce_partials_kernel<<<(pa * pb + 255) / 256, 256, 0, s>>>(part_, nparts_, pa * pb, gram_);
@@ -466,13 +734,70 @@ class BandLanczos {
         f[i] = h;
         f[2 * m + i] = float(buf[i] - double(h));
       }
-      e = cudaMemcpyAsync(coef_, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice, s);
-      if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
-      const float* ch = reinterpret_cast<const float*>(coef_);
-      const float* cl = ch + 2 * m;
       const float bh = float(beta), bl = float(beta - double(bh));
-      block_combine32_kernel<<<grid_for(n_ * pw), kThreads, 0, s>>>(W, out, pw, bh, bl, X1, p1, ch, cl,
-                                                                     X2 ? X2 : X1, p2, ch + m, cl + m, L_, n_);
+      const int K = p1 + p2;
+      if (K <= kCK && pw <= kCN) {
+        // integer slices of the coefficients of [C1; C2] per column (see block_combine_tc_kernel)
+        const int KS = (K + 15) / 16, NT = (pw + 7) / 8;
+        std::vector<uint16_t> sl(size_t(4) * NT * 8 * kCW * 2, 0);
+        std::vector<int> fe(size_t(NT) * 8, 0);
+        for (int j = 0; j < pw; ++j) {
+          double mx = 0.0;
+          for (int k = 0; k < K; ++k)
+            mx = std::max(mx, std::fabs(k < p1 ? buf[size_t(k) * pw + j] : buf[m + size_t(k - p1) * pw + j]));
+          if (!(mx >= 0x1p-119)) continue;   // a zero column (or one below 2^-119): slices stay zero
+          int ex = 0;
+          std::frexp(mx, &ex);                // mx in [2^(ex-1), 2^ex)
+          fe[j] = ex;
+          for (int k = 0; k < K; ++k) {
+            double v = std::ldexp(k < p1 ? buf[size_t(k) * pw + j] : buf[m + size_t(k - p1) * pw + j], 8 - ex);
+            for (int i = 0; i < 4; ++i) {
+              const double qi = std::nearbyint(v);
+              v = (v - qi) * 256.0;
+              // |qi| <= 256: exact in bf16 (sign, exponent, 7 stored bits)
+              const float fq = float(qi);
+              uint32_t bits;
+              std::memcpy(&bits, &fq, 4);
+              sl[(size_t(i) * NT * 8 + j) * kCW * 2 + k] = uint16_t(bits >> 16);
+            }
+          }
+        }
+        uint32_t* dsl = reinterpret_cast<uint32_t*>(coef_);
+        int* dfe = reinterpret_cast<int*>(dsl + size_t(4) * NT * 8 * kCW);
+        e = cudaMemcpyAsync(dsl, sl.data(), sl.size() * 2, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dfe, fe.data(), fe.size() * 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
+        const int grid = int(std::max<int64_t>(1, std::min<int64_t>((n_ + 127) / 128, int64_t(device_sms()) * 8)));
+        const float* x2 = X2 ? X2 : X1;
+#define MCD_COMBINE_TC(ks, nt)                                                                              \
+  block_combine_tc_kernel<ks, nt><<<grid, kThreads, 0, s>>>(W, out, pw, bh, bl, X1, p1, x2, p2, dsl, dfe, L_, n_)
+        switch (KS * 8 + NT) {
+          case 9: MCD_COMBINE_TC(1, 1); break;
+          case 10: MCD_COMBINE_TC(1, 2); break;
+          case 11: MCD_COMBINE_TC(1, 3); break;
+          case 12: MCD_COMBINE_TC(1, 4); break;
+          case 17: MCD_COMBINE_TC(2, 1); break;
+          case 18: MCD_COMBINE_TC(2, 2); break;
+          case 19: MCD_COMBINE_TC(2, 3); break;
+          case 20: MCD_COMBINE_TC(2, 4); break;
+          case 25: MCD_COMBINE_TC(3, 1); break;
+          case 26: MCD_COMBINE_TC(3, 2); break;
+          case 27: MCD_COMBINE_TC(3, 3); break;
+          case 28: MCD_COMBINE_TC(3, 4); break;
+          case 33: MCD_COMBINE_TC(4, 1); break;
+          case 34: MCD_COMBINE_TC(4, 2); break;
+          case 35: MCD_COMBINE_TC(4, 3); break;
+          default: MCD_COMBINE_TC(4, 4); break;
+        }
+#undef MCD_COMBINE_TC
+      } else {
+        e = cudaMemcpyAsync(coef_, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
+        const float* ch = reinterpret_cast<const float*>(coef_);
+        const float* cl = ch + 2 * m;
+        block_combine32_kernel<<<grid_for(n_ * pw), kThreads, 0, s>>>(W, out, pw, bh, bl, X1, p1, ch, cl,
+                                                                       X2 ? X2 : X1, p2, ch + m, cl + m, L_, n_);
+      }
     } else {
       e = cudaMemcpyAsync(coef_, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
