@@ -151,15 +151,30 @@ __device__ __forceinline__ uint32_t bf16_split(float& v) {
   return uint32_t(__bfloat16_as_ushort(h));
 }
 
-// the chunk's rows [r0, r0 + kGR) of columns [0, p) of M as three transposed
-// bf16 slices: word (s, c, kp) holds rows 2 kp (low half) and 2 kp + 1
-__device__ __forceinline__ void gram_stage(const float* __restrict__ M, int p, int ld, int64_t n, int64_t r0,
-                                           uint32_t* sl, int cpad) {
+__device__ __forceinline__ void gram_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+
+// rows [r0, r0 + kGR) of M (ld floats each, contiguous) into raw, as 16-byte
+// copies (the last one may run up to 12 bytes past row n - 1: the blocks are
+// allocated with room for it)
+__device__ __forceinline__ void gram_fetch(const float* __restrict__ M, int ld, int64_t n, int64_t r0, float* raw) {
+  const int64_t rows = (n - r0 < kGR) ? n - r0 : kGR;
+  const int units = int((rows * ld * 4 + 15) / 16);
+  const unsigned char* src = reinterpret_cast<const unsigned char*>(M + r0 * ld);
+  for (int u = threadIdx.x; u < units; u += kThreads)
+    gram_cp16(reinterpret_cast<unsigned char*>(raw) + 16 * u, src + 16 * u);
+}
+
+// the chunk's columns [0, p) as three transposed bf16 slices: word (s, c, kp)
+// holds rows 2 kp (low half) and 2 kp + 1; rows at or past n are zero
+__device__ __forceinline__ void gram_split(const float* raw, int p, int ld, int64_t rows, uint32_t* sl, int cpad) {
   for (int e = threadIdx.x; e < (kGR / 2) * p; e += kThreads) {
     const int kp = e / p, c = e - kp * p;
-    const int64_t ra = r0 + 2 * kp, rb = ra + 1;
-    float va = ra < n ? __ldg(M + ra * ld + c) : 0.f;
-    float vb = rb < n ? __ldg(M + rb * ld + c) : 0.f;
+    float va = 2 * kp < rows ? raw[(2 * kp) * ld + c] : 0.f;
+    float vb = 2 * kp + 1 < rows ? raw[(2 * kp + 1) * ld + c] : 0.f;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
       const uint32_t lo = bf16_split(va), hi = bf16_split(vb);
@@ -168,19 +183,44 @@ __device__ __forceinline__ void gram_stage(const float* __restrict__ M, int p, i
   }
 }
 
+// shared memory of gram_tc_kernel (words): raw rows of one or two matrices,
+// then the slices of X and (unless Y is X) of Y
+struct GramSmem {
+  int Mp, Np, kparts, raw_words, xs_words, ys_words;
+  bool same;
+  __host__ __device__ GramSmem(int pa, int pb, int ld, bool same_) {
+    same = same_;
+    Mp = (pa + 15) / 16 * 16;
+    Np = (pb + 7) / 8 * 8;
+    const int nblk = ((Mp / 16 + 1) / 2) * ((Np / 8 + 1) / 2);
+    kparts = nblk >= 5 ? 1 : (nblk >= 3 ? 2 : (nblk == 2 ? 4 : 8));
+    raw_words = (same ? 1 : 2) * kGR * ld;
+    xs_words = 3 * Mp * kGW;
+    ys_words = same ? 0 : 3 * Np * kGW;
+  }
+  __host__ __device__ size_t bytes() const {
+    const size_t main = size_t(raw_words + xs_words + ys_words) * 4;
+    const size_t red = size_t(kparts) * Mp * Np * 8;
+    return main > red ? main : red;
+  }
+};
+
 __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const float* __restrict__ X, int pa,
                                                            const float* __restrict__ Y, int pb, int ld, int64_t n,
                                                            double* partials) {
   extern __shared__ __align__(16) uint32_t s_gram[];
-  const int Mt = (pa + 15) / 16, Nt = (pb + 7) / 8;
-  const int Mp = Mt * 16, Np = Nt * 8;
-  uint32_t* xs = s_gram;                       // [3][Mp][kGW]
-  uint32_t* ys = s_gram + 3 * Mp * kGW;        // [3][Np][kGW]
-  for (int i = threadIdx.x; i < 3 * (Mp + Np) * kGW; i += kThreads) s_gram[i] = 0u;   // padding stays zero
+  const GramSmem L(pa, pb, ld, X == Y && pa == pb);
+  const int Mt = L.Mp / 16, Nt = L.Np / 8, Mp = L.Mp;
+  float* raw_x = reinterpret_cast<float*>(s_gram);
+  float* raw_y = L.same ? raw_x : raw_x + kGR * ld;
+  uint32_t* xs = s_gram + L.raw_words;                           // [3][Mp][kGW]
+  uint32_t* ys = L.same ? xs : xs + L.xs_words;                  // [3][yst][kGW]
+  const int yst = L.same ? Mp : L.Np;
+  for (int i = threadIdx.x; i < L.xs_words + L.ys_words; i += kThreads) xs[i] = 0u;   // padding stays zero
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const int nmb = (Mt + 1) / 2, nnb = (Nt + 1) / 2, nblk = nmb * nnb;
-  const int kparts = nblk >= 5 ? 1 : (nblk >= 3 ? 2 : (nblk == 2 ? 4 : 8));
+  const int nnb = (Nt + 1) / 2, nblk = ((Mt + 1) / 2) * nnb;
+  const int kparts = L.kparts;
   const bool busy = warp < nblk * kparts;
   const int blk = warp % nblk, kp = warp / nblk;
   const int mt0 = (blk / nnb) * 2, nt0 = (blk % nnb) * 2;
@@ -193,11 +233,25 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const float* __restri
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = dh[i][j][q] = dl[i][j][q] = 0.f;
-  for (int64_t r0 = int64_t(blockIdx.x) * kGR; r0 < n; r0 += int64_t(gridDim.x) * kGR) {
-    __syncthreads();   // the previous chunk's slices are consumed
-    gram_stage(X, pa, ld, n, r0, xs, Mp);
-    gram_stage(Y, pb, ld, n, r0, ys, Np);
-    __syncthreads();
+  const int64_t step = int64_t(gridDim.x) * kGR;
+  int64_t r0 = int64_t(blockIdx.x) * kGR;
+  if (r0 < n) {
+    gram_fetch(X, ld, n, r0, raw_x);
+    if (!L.same) gram_fetch(Y, ld, n, r0, raw_y);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (; r0 < n; r0 += step) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();   // the chunk's rows have landed; the previous chunk's slices are consumed
+    const int64_t rows = (n - r0 < kGR) ? n - r0 : kGR;
+    gram_split(raw_x, pa, ld, rows, xs, Mp);
+    if (!L.same) gram_split(raw_y, pb, ld, rows, ys, yst);
+    __syncthreads();   // slices ready, raw rows free: the next chunk loads during the products
+    if (r0 + step < n) {
+      gram_fetch(X, ld, n, r0 + step, raw_x);
+      if (!L.same) gram_fetch(Y, ld, n, r0 + step, raw_y);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
     if (!busy) continue;
     for (int ks = ks0; ks < ks0 + ksteps; ++ks) {
       const int kw = ks * 8 + t;   // word of rows 16 ks + 2t, 2t + 1
@@ -218,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const float* __restri
           uint32_t b[2][2];
 #pragma unroll
           for (int ni = 0; ni < 2; ++ni) {
-            const uint32_t* base = ys + (j * Np + (nt0 + ni) * 8 + g) * kGW + kw;
+            const uint32_t* base = ys + (j * yst + (nt0 + ni) * 8 + g) * kGW + kw;
             const bool ok = nt0 + ni < Nt;
             b[ni][0] = ok ? base[0] : 0u;
             b[ni][1] = ok ? base[4] : 0u;
@@ -242,9 +296,11 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const float* __restri
           acc[mi][ni][q] = 0.f;
         }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   // CTA partial: the warps' entries (fp64) by split, summed in split order
   __syncthreads();
   double* red = reinterpret_cast<double*>(s_gram);   // [kparts][Mp][Np]
+  const int Np = L.Np;
   if (busy) {
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi)
@@ -267,16 +323,6 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(const float* __restri
     for (int k = 0; k < kparts; ++k) v += red[(int64_t(k) * Mp + ia) * Np + ib];
     partials[int64_t(blockIdx.x) * npair + pr] = v;
   }
-}
-
-// shared memory of gram_tc_kernel for pa x pb
-size_t gram_tc_smem(int pa, int pb) {
-  const int Mp = (pa + 15) / 16 * 16, Np = (pb + 7) / 8 * 8;
-  const int nblk = ((Mp / 16 + 1) / 2) * ((Np / 8 + 1) / 2);
-  const int kparts = nblk >= 5 ? 1 : (nblk >= 3 ? 2 : (nblk == 2 ? 4 : 8));
-  const size_t slices = size_t(3) * (Mp + Np) * kGW * 4;
-  const size_t red = size_t(kparts) * Mp * Np * 8;
-  return std::max(slices, red);
 }
 
 __global__ void reduce_partials_kernel(const double* partials, int nparts, int npair, double* out) {
@@ -456,7 +502,15 @@ __global__ void __launch_bounds__(kThreads, 1) block_combine_tc_kernel(const flo
         const int j = nt * 8 + 2 * t + (q & 1);
         if (r >= n || j >= pw) continue;
         const int sh = er[h] + s_f[j] - 16;
-        float hi = ldexpf(oh[nt][q], sh), lo = ldexpf(ol[nt][q], sh);
+        float hi, lo;
+        if (sh >= -126 && sh <= 127) {   // a power of two: exact
+          const float f = __uint_as_float(uint32_t(127 + sh) << 23);
+          hi = oh[nt][q] * f;
+          lo = ol[nt][q] * f;
+        } else {
+          hi = ldexpf(oh[nt][q], sh);
+          lo = ldexpf(ol[nt][q], sh);
+        }
         if (bh != 0.f || bl != 0.f) df_add(hi, lo, W[r * ld + j], bh, bl);
         out[r * ld + j] = hi + lo;
       }
@@ -699,7 +753,7 @@ class BandLanczos {
   int gram(const T* X, int pa, const T* Y, int pb, std::vector<double>& G) {
     cudaStream_t s = c_->stream;
     if constexpr (sizeof(T) == 4) {
-      const size_t smem = gram_tc_smem(pa, pb);
+      const size_t smem = GramSmem(pa, pb, L_, X == Y && pa == pb).bytes();
       if (smem > 48 * 1024) {
         const cudaError_t ea =
             cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

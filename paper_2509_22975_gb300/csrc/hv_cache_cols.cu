@@ -670,6 +670,20 @@ cudaError_t pick_and_apply(mcd_ctx* c, const void* x, void* y, int ncols, int ld
     }
   cudaError_t e = cache_items_prepare(c, ncols, dtype);
   if (e != cudaSuccess) return e;
+  // where more than a tenth of a pass's work items have stage ranges too long
+  // for even one 16-byte column chunk in the x buffer, the tiles gather those
+  // rows from L2 and lose to the CTA-per-item kernel (3x on the 6x4 basis):
+  // no trial then
+  for (int pass = 0; pass < 2; ++pass) {
+    const std::vector<uint2>& rng = c->stage_range[pass];
+    size_t direct = 0;
+    for (const uint2& r : rng)
+      if ((int64_t(r.y) - r.x + 1) * 16 > kTXBytes) ++direct;
+    if (direct * 10 > rng.size()) {
+      pick = 2;
+      return cache_apply_items(c, x, y, ncols, ld, dtype, used);
+    }
+  }
   bool u1 = false, u2 = false;
   e = cudaEventRecord(c->tune_ev[0], s);
   if (e == cudaSuccess) e = apply_tiles(c, x, y, ncols, ld, dtype, &u1);   // also builds its work units
