@@ -171,8 +171,15 @@ __device__ __forceinline__ void gram_fetch(const float* __restrict__ M, int ld, 
 // the chunk's columns [0, p) as three transposed bf16 slices: word (s, c, kp)
 // holds rows 2 kp (low half) and 2 kp + 1; rows at or past n are zero
 __device__ __forceinline__ void gram_split(const float* raw, int p, int ld, int64_t rows, uint32_t* sl, int cpad) {
-  for (int e = threadIdx.x; e < (kGR / 2) * p; e += kThreads) {
-    const int kp = e / p, c = e - kp * p;
+  // element e = kp p + c, stepping e by kThreads without a division per step
+  const int dk = kThreads / p, dc = kThreads - dk * p;
+  int kp = threadIdx.x / p, c = threadIdx.x - kp * p;
+  for (; kp < kGR / 2; kp += dk, c += dc) {
+    if (c >= p) {
+      c -= p;
+      ++kp;
+      if (kp >= kGR / 2) break;
+    }
     float va = 2 * kp < rows ? raw[(2 * kp) * ld + c] : 0.f;
     float vb = 2 * kp + 1 < rows ? raw[(2 * kp + 1) * ld + c] : 0.f;
 #pragma unroll
@@ -205,7 +212,7 @@ struct GramSmem {
   }
 };
 
-__global__ void __launch_bounds__(kThreads) gram_tc_kernel(const float* __restrict__ X, int pa,
+__global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const float* __restrict__ X, int pa,
                                                            const float* __restrict__ Y, int pb, int ld, int64_t n,
                                                            double* partials) {
   extern __shared__ __align__(16) uint32_t s_gram[];
@@ -397,7 +404,7 @@ __device__ __forceinline__ void combine_tc_load(const float* __restrict__ X1, in
 }
 
 template <int KS, int NT>
-__global__ void __launch_bounds__(kThreads, 1) block_combine_tc_kernel(const float* W, float* out, int pw, float bh,
+__global__ void __launch_bounds__(kThreads, 2) block_combine_tc_kernel(const float* W, float* out, int pw, float bh,
                                                                        float bl, const float* __restrict__ X1, int p1,
                                                                        const float* __restrict__ X2, int p2,
                                                                        const uint32_t* __restrict__ cslices,
@@ -439,19 +446,10 @@ __global__ void __launch_bounds__(kThreads, 1) block_combine_tc_kernel(const flo
 #pragma unroll
         for (int q = 0; q < 4; ++q) v[h][ks][q] *= sc;   // exact: |v| < 256
     }
-    // slice by slice (q = rint(v), v <- 256 (v - q), both exact): the MMA sums
-    // the products with the coefficient slices j <= 3 - i into the level
-    // i + j accumulator, exact fp32 integers
-    float acc[4][NT][4];
+    // the four slices as A fragments (q = rint(v), v <- 256 (v - q), both exact)
+    uint32_t a[4][KS][4];
 #pragma unroll
-    for (int l = 0; l < 4; ++l)
-#pragma unroll
-      for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[l][nt][q] = 0.f;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      uint32_t a[KS][4];
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int ks = 0; ks < KS; ++ks) {
         uint32_t qb[2][4];
@@ -463,57 +461,57 @@ __global__ void __launch_bounds__(kThreads, 1) block_combine_tc_kernel(const flo
             v[h][ks][q] = __fmul_rn(__fsub_rn(v[h][ks][q], qi), 256.f);
             qb[h][q] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(qi)));
           }
-        a[ks][0] = qb[0][0] | (qb[0][1] << 16);
-        a[ks][1] = qb[1][0] | (qb[1][1] << 16);
-        a[ks][2] = qb[0][2] | (qb[0][3] << 16);
-        a[ks][3] = qb[1][2] | (qb[1][3] << 16);
+        a[i][ks][0] = qb[0][0] | (qb[0][1] << 16);
+        a[i][ks][1] = qb[1][0] | (qb[1][1] << 16);
+        a[i][ks][2] = qb[0][2] | (qb[0][3] << 16);
+        a[i][ks][3] = qb[1][2] | (qb[1][3] << 16);
       }
+    // the next tile's values load while this one is multiplied
+    if (tile + stride < ntile) combine_tc_load<KS>(X1, p1, X2, K, ld, n, (tile + stride) * 16, g, t, v);
+    // one 8-column tile at a time: the MMA sums the slice products with
+    // i + j = l into the level-l accumulator (exact fp32 integers); the
+    // levels then go into a double-float with weight 2^(-8 l)
+#pragma unroll 1
+    for (int nt = 0; nt < NT; ++nt) {
+      float acc[4][4];
 #pragma unroll
-      for (int j = 0; i + j < 4; ++j)
+      for (int l = 0; l < 4; ++l)
 #pragma unroll
-        for (int ks = 0; ks < KS; ++ks)
+        for (int q = 0; q < 4; ++q) acc[l][q] = 0.f;
 #pragma unroll
-          for (int nt = 0; nt < NT; ++nt) {
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; i + j < 4; ++j)
+#pragma unroll
+          for (int ks = 0; ks < KS; ++ks) {
             const uint32_t* bp = s_c + (j * NT * 8 + nt * 8 + g) * kCW + ks * 8 + t;
             const uint32_t b[2] = {bp[0], bp[4]};
-            mma_bf16_16816(acc[i + j][nt], a[ks], b);
+            mma_bf16_16816(acc[i + j], a[i][ks], b);
           }
-    }
-    // the next tile's values load while this one's results are formed
-    if (tile + stride < ntile) combine_tc_load<KS>(X1, p1, X2, K, ld, n, (tile + stride) * 16, g, t, v);
-    // the levels in double-float, weight 2^(-8 l)
-    float oh[NT][4], ol[NT][4];
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        oh[nt][q] = acc[0][nt][q];
-        ol[nt][q] = 0.f;
-        df_add(oh[nt][q], ol[nt][q], __fmul_rn(acc[1][nt][q], 0x1p-8f));
-        df_add(oh[nt][q], ol[nt][q], __fmul_rn(acc[2][nt][q], 0x1p-16f));
-        df_add(oh[nt][q], ol[nt][q], __fmul_rn(acc[3][nt][q], 0x1p-24f));
-      }
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int h = q >> 1;
         const int64_t r = r0 + g + 8 * h;
         const int j = nt * 8 + 2 * t + (q & 1);
         if (r >= n || j >= pw) continue;
+        float oh = acc[0][q], ol = 0.f;
+        df_add(oh, ol, __fmul_rn(acc[1][q], 0x1p-8f));
+        df_add(oh, ol, __fmul_rn(acc[2][q], 0x1p-16f));
+        df_add(oh, ol, __fmul_rn(acc[3][q], 0x1p-24f));
         const int sh = er[h] + s_f[j] - 16;
         float hi, lo;
         if (sh >= -126 && sh <= 127) {   // a power of two: exact
           const float f = __uint_as_float(uint32_t(127 + sh) << 23);
-          hi = oh[nt][q] * f;
-          lo = ol[nt][q] * f;
+          hi = oh * f;
+          lo = ol * f;
         } else {
-          hi = ldexpf(oh[nt][q], sh);
-          lo = ldexpf(ol[nt][q], sh);
+          hi = ldexpf(oh, sh);
+          lo = ldexpf(ol, sh);
         }
         if (bh != 0.f || bl != 0.f) df_add(hi, lo, W[r * ld + j], bh, bl);
         out[r * ld + j] = hi + lo;
       }
+    }
   }
 }
 
