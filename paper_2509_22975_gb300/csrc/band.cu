@@ -144,11 +144,20 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// bf16 bits of round-to-nearest(v), and v minus that value (exact)
-__device__ __forceinline__ uint32_t bf16_split(float& v) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  v = __fsub_rn(v, __bfloat162float(h));
-  return uint32_t(__bfloat16_as_ushort(h));
+// round-to-nearest bf16 of (va, vb) as one word (va in the low half), and
+// va, vb minus those values (exact)
+__device__ __forceinline__ uint32_t bf16x2_split(float& va, float& vb) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(va, vb);
+  const uint32_t w = *reinterpret_cast<const uint32_t*>(&h);
+  va = __fsub_rn(va, __uint_as_float(w << 16));
+  vb = __fsub_rn(vb, __uint_as_float(w & 0xFFFF0000u));
+  return w;
+}
+
+// two exact bf16 integers (|q| <= 256) as one word, qa in the low half
+__device__ __forceinline__ uint32_t bf16x2_pack(float qa, float qb) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(qa, qb);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
 
 __device__ __forceinline__ void gram_cp16(void* dst, const void* src) {
@@ -183,10 +192,7 @@ __device__ __forceinline__ void gram_split(const float* raw, int p, int ld, int6
     float va = 2 * kp < rows ? raw[(2 * kp) * ld + c] : 0.f;
     float vb = 2 * kp + 1 < rows ? raw[(2 * kp + 1) * ld + c] : 0.f;
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      const uint32_t lo = bf16_split(va), hi = bf16_split(vb);
-      sl[(s * cpad + c) * kGW + kp] = lo | (hi << 16);
-    }
+    for (int s = 0; s < 3; ++s) sl[(s * cpad + c) * kGW + kp] = bf16x2_split(va, vb);
   }
 }
 
@@ -452,19 +458,18 @@ __global__ void __launch_bounds__(kThreads, 2) block_combine_tc_kernel(const flo
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int ks = 0; ks < KS; ++ks) {
-        uint32_t qb[2][4];
+        float qi[2][4];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float qi = rintf(v[h][ks][q]);
-            v[h][ks][q] = __fmul_rn(__fsub_rn(v[h][ks][q], qi), 256.f);
-            qb[h][q] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(qi)));
+            qi[h][q] = rintf(v[h][ks][q]);
+            v[h][ks][q] = __fmul_rn(__fsub_rn(v[h][ks][q], qi[h][q]), 256.f);
           }
-        a[i][ks][0] = qb[0][0] | (qb[0][1] << 16);
-        a[i][ks][1] = qb[1][0] | (qb[1][1] << 16);
-        a[i][ks][2] = qb[0][2] | (qb[0][3] << 16);
-        a[i][ks][3] = qb[1][2] | (qb[1][3] << 16);
+        a[i][ks][0] = bf16x2_pack(qi[0][0], qi[0][1]);
+        a[i][ks][1] = bf16x2_pack(qi[1][0], qi[1][1]);
+        a[i][ks][2] = bf16x2_pack(qi[0][2], qi[0][3]);
+        a[i][ks][3] = bf16x2_pack(qi[1][2], qi[1][3]);
       }
     // the next tile's values load while this one is multiplied
     if (tile + stride < ntile) combine_tc_load<KS>(X1, p1, X2, K, ld, n, (tile + stride) * 16, g, t, v);
