@@ -144,6 +144,14 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// four 8x8 bf16 matrices from shared memory; lane L gives the address of row
+// L % 8 of matrix L / 8, register j receives matrix j in the MMA fragment layout
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const uint32_t* row) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(row))));
+}
+
 // round-to-nearest bf16 of (va, vb) as one word (va in the low half), and
 // va, vb minus those values (exact)
 __device__ __forceinline__ uint32_t bf16x2_split(float& va, float& vb) {
@@ -178,36 +186,38 @@ __device__ __forceinline__ void gram_fetch(const float* __restrict__ M, int ld, 
 }
 
 // the chunk's columns [0, p) as three transposed bf16 slices: word (s, c, kp)
-// holds rows 2 kp (low half) and 2 kp + 1; rows at or past n are zero
-__device__ __forceinline__ void gram_split(const float* raw, int p, int ld, int64_t rows, uint32_t* sl, int cpad) {
-  // element e = kp p + c, stepping e by kThreads without a division per step
-  const int dk = kThreads / p, dc = kThreads - dk * p;
-  int kp = threadIdx.x / p, c = threadIdx.x - kp * p;
-  for (; kp < kGR / 2; kp += dk, c += dc) {
-    if (c >= p) {
-      c -= p;
-      ++kp;
-      if (kp >= kGR / 2) break;
-    }
+// holds rows 2 kp (low half) and 2 kp + 1; rows at or past n are zero.  A warp
+// takes tiles of 8 columns x 4 row pairs, lane = (column lane / 4, pair lane %
+// 4): its stores (bank 4 c + kp, the word stride being 4 mod 32) hit 32 banks.
+__device__ __forceinline__ void gram_split(const float* raw, int p, int ld, int64_t rows, uint32_t* sl, int cpad,
+                                           int c0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nct = (p + 7) / 8;
+  const int cl = lane >> 2, kl = lane & 3;
+  for (int tile = warp; tile < nct * (kGR / 8); tile += kThreads / 32) {
+    const int kb = tile / nct;
+    const int c = (tile - kb * nct) * 8 + cl, kp = kb * 4 + kl;
+    if (c >= p) continue;
     float va = 2 * kp < rows ? raw[(2 * kp) * ld + c] : 0.f;
     float vb = 2 * kp + 1 < rows ? raw[(2 * kp + 1) * ld + c] : 0.f;
-#pragma unroll
-    for (int s = 0; s < 3; ++s) sl[(s * cpad + c) * kGW + kp] = bf16x2_split(va, vb);
+    sl[(c0 + c) * kGW + kp] = bf16x2_split(va, vb);
+    sl[(cpad + c0 + c) * kGW + kp] = bf16x2_split(va, vb);
+    sl[(2 * cpad + c0 + c) * kGW + kp] = bf16x2_pack(va, vb);   // the exact remainder
   }
 }
 
-// shared memory of gram_tc_kernel (words): raw rows of one or two matrices,
-// then the slices of X and (unless Y is X) of Y
+// shared memory of gram_tc_kernel (words): raw rows of X1, X2 (if any) and
+// Y (unless Y is X1), then the slices of X = [X1 X2] and (unless Y is X1) of Y
 struct GramSmem {
   int Mp, Np, kparts, raw_words, xs_words, ys_words;
   bool same;
-  __host__ __device__ GramSmem(int pa, int pb, int ld, bool same_) {
+  __host__ __device__ GramSmem(int pa, int pb, int ld, bool same_, bool two) {
     same = same_;
     Mp = (pa + 15) / 16 * 16;
     Np = (pb + 7) / 8 * 8;
     const int nblk = ((Mp / 16 + 1) / 2) * ((Np / 8 + 1) / 2);
     kparts = nblk >= 5 ? 1 : (nblk >= 3 ? 2 : (nblk == 2 ? 4 : 8));
-    raw_words = (same ? 1 : 2) * kGR * ld;
+    raw_words = (1 + (two ? 1 : 0) + (same ? 0 : 1)) * kGR * ld;
     xs_words = 3 * Mp * kGW;
     ys_words = same ? 0 : 3 * Np * kGW;
   }
@@ -218,14 +228,20 @@ struct GramSmem {
   }
 };
 
-__global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const float* __restrict__ X, int pa,
-                                                           const float* __restrict__ Y, int pb, int ld, int64_t n,
-                                                           double* partials) {
+// G = [X1 X2]^T Y (pa = pa1 + pa2 rows: X1's columns, then X2's; X2 may be
+// null with pa2 = 0); Y = X1 with pb = pa1 shares X1's slices.
+__global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const float* __restrict__ X1, int pa1,
+                                                              const float* __restrict__ X2, int pa2,
+                                                              const float* __restrict__ Y, int pb, int ld, int64_t n,
+                                                              double* partials) {
   extern __shared__ __align__(16) uint32_t s_gram[];
-  const GramSmem L(pa, pb, ld, X == Y && pa == pb);
+  const int pa = pa1 + pa2;
+  const bool two = pa2 > 0;
+  const GramSmem L(pa, pb, ld, Y == X1 && pb == pa1, two);
   const int Mt = L.Mp / 16, Nt = L.Np / 8, Mp = L.Mp;
   float* raw_x = reinterpret_cast<float*>(s_gram);
-  float* raw_y = L.same ? raw_x : raw_x + kGR * ld;
+  float* raw_x2 = raw_x + kGR * ld;
+  float* raw_y = L.same ? raw_x : raw_x + (two ? 2 : 1) * kGR * ld;
   uint32_t* xs = s_gram + L.raw_words;                           // [3][Mp][kGW]
   uint32_t* ys = L.same ? xs : xs + L.xs_words;                  // [3][yst][kGW]
   const int yst = L.same ? Mp : L.Np;
@@ -249,7 +265,8 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const float* __res
   const int64_t step = int64_t(gridDim.x) * kGR;
   int64_t r0 = int64_t(blockIdx.x) * kGR;
   if (r0 < n) {
-    gram_fetch(X, ld, n, r0, raw_x);
+    gram_fetch(X1, ld, n, r0, raw_x);
+    if (two) gram_fetch(X2, ld, n, r0, raw_x2);
     if (!L.same) gram_fetch(Y, ld, n, r0, raw_y);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
@@ -257,44 +274,45 @@ __global__ void __launch_bounds__(kThreads, 2) gram_tc_kernel(const float* __res
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();   // the chunk's rows have landed; the previous chunk's slices are consumed
     const int64_t rows = (n - r0 < kGR) ? n - r0 : kGR;
-    gram_split(raw_x, pa, ld, rows, xs, Mp);
-    if (!L.same) gram_split(raw_y, pb, ld, rows, ys, yst);
+    gram_split(raw_x, pa1, ld, rows, xs, Mp, 0);
+    if (two) gram_split(raw_x2, pa2, ld, rows, xs, Mp, pa1);
+    if (!L.same) gram_split(raw_y, pb, ld, rows, ys, yst, 0);
     __syncthreads();   // slices ready, raw rows free: the next chunk loads during the products
     if (r0 + step < n) {
-      gram_fetch(X, ld, n, r0 + step, raw_x);
+      gram_fetch(X1, ld, n, r0 + step, raw_x);
+      if (two) gram_fetch(X2, ld, n, r0 + step, raw_x2);
       if (!L.same) gram_fetch(Y, ld, n, r0 + step, raw_y);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     if (!busy) continue;
+    // fragment rows of this lane for ldmatrix: A (row-major m x k) matrices
+    // (m lo, k lo), (m hi, k lo), (m lo, k hi), (m hi, k hi); B (n x k) matrices
+    // (n tile 0, k lo), (n tile 0, k hi), (n tile 1, k lo), (n tile 1, k hi).
+    // Rows of tiles past the matrix are clamped to its last row (their products
+    // are not formed).
+    const int lr = lane & 7, lm = lane >> 3;
+    int arow[2], brow;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi) arow[mi] = min((mt0 + mi) * 16 + lr + (lm & 1) * 8, Mp - 1);
+    brow = min(nt0 * 8 + (lm >> 1) * 8 + lr, Nt * 8 - 1);
+    const int akoff = (lm >> 1) * 4, bkoff = (lm & 1) * 4;   // words of the k hi half
     for (int ks = ks0; ks < ks0 + ksteps; ++ks) {
-      const int kw = ks * 8 + t;   // word of rows 16 ks + 2t, 2t + 1
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         uint32_t a[2][4];
 #pragma unroll
-        for (int mi = 0; mi < 2; ++mi) {
-          const uint32_t* base = xs + (i * Mp + (mt0 + mi) * 16 + g) * kGW + kw;
-          const bool ok = mt0 + mi < Mt;
-          a[mi][0] = ok ? base[0] : 0u;
-          a[mi][1] = ok ? base[8 * kGW] : 0u;
-          a[mi][2] = ok ? base[4] : 0u;
-          a[mi][3] = ok ? base[8 * kGW + 4] : 0u;
-        }
+        for (int mi = 0; mi < 2; ++mi) ldmatrix_x4(a[mi], xs + (i * Mp + arow[mi]) * kGW + ks * 8 + akoff);
 #pragma unroll
         for (int j = 0; i + j < 3; ++j) {
-          uint32_t b[2][2];
+          uint32_t b[4];
+          ldmatrix_x4(b, ys + (j * yst + brow) * kGW + ks * 8 + bkoff);
+          const uint32_t b0[2] = {b[0], b[1]}, b1[2] = {b[2], b[3]};
 #pragma unroll
-          for (int ni = 0; ni < 2; ++ni) {
-            const uint32_t* base = ys + (j * yst + (nt0 + ni) * 8 + g) * kGW + kw;
-            const bool ok = nt0 + ni < Nt;
-            b[ni][0] = ok ? base[0] : 0u;
-            b[ni][1] = ok ? base[4] : 0u;
+          for (int mi = 0; mi < 2; ++mi) {
+            if (mt0 + mi >= Mt) continue;
+            mma_bf16_16816(acc[mi][0], a[mi], b0);
+            if (nt0 + 1 < Nt) mma_bf16_16816(acc[mi][1], a[mi], b1);
           }
-#pragma unroll
-          for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-            for (int ni = 0; ni < 2; ++ni)
-              if (mt0 + mi < Mt && nt0 + ni < Nt) mma_bf16_16816(acc[mi][ni], a[mi], b[ni]);
         }
       }
     }
@@ -754,24 +772,54 @@ class BandLanczos {
 
   // host G = X[:, :pa]^T Y[:, :pb]
   int gram(const T* X, int pa, const T* Y, int pb, std::vector<double>& G) {
+    return gram2(X, pa, nullptr, 0, Y, pb, G);
+  }
+
+  // host G = [X1[:, :pa1] X2[:, :pa2]]^T Y[:, :pb] ((pa1 + pa2) x pb, X1's
+  // rows first): one pass over the rows in fp32 when pa1 + pa2 <= 64
+  int gram2(const T* X1, int pa1, const T* X2, int pa2, const T* Y, int pb, std::vector<double>& G) {
     cudaStream_t s = c_->stream;
+    const int pa = pa1 + pa2;
     if constexpr (sizeof(T) == 4) {
-      const size_t smem = GramSmem(pa, pb, L_, X == Y && pa == pb).bytes();
-      if (smem > 48 * 1024) {
-        const cudaError_t ea =
-            cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (ea != cudaSuccess) return cuda_fail(c_, ea, "Gram kernel shared memory");
+      if (pa <= kMaxOrb) {
+        const size_t smem = GramSmem(pa, pb, L_, Y == X1 && pb == pa1, pa2 > 0).bytes();
+        if (smem > 48 * 1024) {
+          const cudaError_t ea =
+              cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+          if (ea != cudaSuccess) return cuda_fail(c_, ea, "Gram kernel shared memory");
+        }
+        gram_tc_kernel<<<nparts_, kThreads, smem, s>>>(X1, pa1, pa2 ? X2 : nullptr, pa2, Y, pb, L_, n_, part_);
+        MCD_LAUNCHED(c_);
+        reduce_partials_kernel<<<(pa * pb + 255) / 256, 256, 0, s>>>(part_, nparts_, pa * pb, gram_);
+        MCD_LAUNCHED(c_);
+        G.resize(size_t(pa) * pb);
+        cudaError_t e = cudaMemcpyAsync(G.data(), gram_, sizeof(double) * pa * pb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e == cudaSuccess ? MCD_OK : cuda_fail(c_, e, "Gram");
       }
-      gram_tc_kernel<<<nparts_, kThreads, smem, s>>>(X, pa, Y, pb, L_, n_, part_);
-    } else
-      gram_kernel<T><<<nparts_, kThreads, 0, s>>>(X, pa, Y, pb, L_, n_, part_);
-    MCD_LAUNCHED(c_);
-    reduce_partials_kernel<<<(pa * pb + 255) / 256, 256, 0, s>>>(part_, nparts_, pa * pb, gram_);
-    MCD_LAUNCHED(c_);
-    G.resize(size_t(pa) * pb);
-    cudaError_t e = cudaMemcpyAsync(G.data(), gram_, sizeof(double) * pa * pb, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    return e == cudaSuccess ? MCD_OK : cuda_fail(c_, e, "Gram");
+    }
+    // one product at a time (fp64 vectors, or more than 64 rows)
+    std::vector<double> G1, G2;
+    if constexpr (sizeof(T) == 8) {
+      gram_kernel<T><<<nparts_, kThreads, 0, s>>>(X1, pa1, Y, pb, L_, n_, part_);
+      MCD_LAUNCHED(c_);
+      reduce_partials_kernel<<<(pa1 * pb + 255) / 256, 256, 0, s>>>(part_, nparts_, pa1 * pb, gram_);
+      MCD_LAUNCHED(c_);
+      G1.resize(size_t(pa1) * pb);
+      cudaError_t e = cudaMemcpyAsync(G1.data(), gram_, sizeof(double) * pa1 * pb, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(c_, e, "Gram");
+    } else {
+      const int st = gram2(X1, pa1, nullptr, 0, Y, pb, G1);
+      if (st) return st;
+    }
+    if (pa2) {
+      const int st = gram2(X2, pa2, nullptr, 0, Y, pb, G2);
+      if (st) return st;
+    }
+    G = G1;
+    G.insert(G.end(), G2.begin(), G2.end());
+    return MCD_OK;
   }
 
   // out = beta W + X1 C1 + X2 C2 (C1: p1 x pw, C2: p2 x pw)
@@ -934,15 +982,15 @@ class BandLanczos {
       }
       st = hv_apply(c_, Vcur, W, p, L_, sizeof(T) == 8 ? MCD_F64 : MCD_F32, nullptr, 0);
       if (st) return st;
-      std::vector<double> Gw;
-      st = gram(W, p, W, p, Gw);
+      // [W Vcur]^T W in one pass: the norms of W's columns (their size before
+      // orthogonalisation, for deflation) and A = Vcur^T W
+      std::vector<double> GA;
+      st = gram2(W, p, Vcur, p, W, p, GA);
       if (st) return st;
       std::vector<double> refk(p);
-      for (int j = 0; j < p; ++j) refk[j] = std::sqrt(std::max(Gw[size_t(j) * p + j], 0.0));
-      // A = Vcur^T W ; W -= Vcur A + Vprev B_k^T
-      std::vector<double> A, C1, C2;
-      st = gram(Vcur, p, W, p, A);
-      if (st) return st;
+      for (int j = 0; j < p; ++j) refk[j] = std::sqrt(std::max(GA[size_t(j) * p + j], 0.0));
+      // W -= Vcur A + Vprev B_k^T
+      std::vector<double> A(GA.begin() + size_t(p) * p, GA.begin() + size_t(2) * p * p), C1, C2;
       std::vector<double> Bt;   // p_{k-1} x p_k
       if (pprev) {
         Bt.assign(size_t(pprev) * p, 0.0);
@@ -953,13 +1001,12 @@ class BandLanczos {
       for (size_t i = 0; i < A.size(); ++i) mA[i] = -A[i];
       st = combine(W, W, p, 1.0, Vcur, p, mA, pprev ? Vprev : nullptr, pprev, Bt);
       if (st) return st;
-      // second Gram-Schmidt pass against the window
-      st = gram(Vcur, p, W, p, C1);
+      // second Gram-Schmidt pass against the window: [Vcur Vprev]^T W in one pass
+      std::vector<double> C12;
+      st = gram2(Vcur, p, pprev ? Vprev : nullptr, pprev, W, p, C12);
       if (st) return st;
-      if (pprev) {
-        st = gram(Vprev, pprev, W, p, C2);
-        if (st) return st;
-      }
+      C1.assign(C12.begin(), C12.begin() + size_t(p) * p);
+      C2.assign(C12.begin() + size_t(p) * p, C12.end());
       std::vector<double> mC1(C1.size()), mC2(C2.size());
       for (size_t i = 0; i < C1.size(); ++i) mC1[i] = -C1[i];
       for (size_t i = 0; i < C2.size(); ++i) mC2[i] = -C2[i];
