@@ -129,6 +129,16 @@ typedef enum { MCD_F64 = 0, MCD_F32 = 1 } mcd_dtype;
                                    every value; the Lanczos scalars <v, Hv>
                                    are summed in another order (within
                                    rounding). */
+#define MCD_OPT_BATCH_MODE 12   /* mcd_batch_lanczos_ground, read from the
+                                   first context: 0 = every instance's own
+                                   solve (mcd_lanczos_ground, with its
+                                   connection cache) on a pool of host
+                                   threads, each with its own stream: the
+                                   results of separate calls, bit for bit
+                                   (default); 1 = one sequence of launches
+                                   over all instances in lockstep (the
+                                   matrix-free batched H*v, CUDA-graph
+                                   replay; instances of one site count). */
 #define MCD_OPT_HASH_ITEM 4     /* states per work item of the hash-lookup
                                    kernels: a power of two in [64, 4096]
                                    (default 1024).  Blocks of more states are

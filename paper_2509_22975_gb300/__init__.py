@@ -24,7 +24,8 @@ MCD_OPT_SAMPLER_DEVICE = 5
 MCD_OPT_HV_CACHE = 6
 MCD_OPT_APPLY_SYNC, MCD_OPT_WAIT_TEST, MCD_OPT_KRYLOV_STORE, MCD_OPT_HV_COLS = 7, 8, 9, 10
 HV_COLS_AUTO, HV_COLS_TILES, HV_COLS_ITEMS = 0, 1, 2
-MCD_OPT_BATCH_SPLIT = 11
+MCD_OPT_BATCH_SPLIT, MCD_OPT_BATCH_MODE = 11, 12
+BATCH_POOL, BATCH_LOCKSTEP = 0, 1
 MCD_E_NOT_CONVERGED, MCD_E_TIMEOUT = -5, -7
 CACHE_AUTO, CACHE_OFF, CACHE_REQUIRED = 0, 1, 2
 SAMPLER_AUTO, SAMPLER_HOST, SAMPLER_DEVICE = 0, 1, 2
@@ -153,8 +154,9 @@ def mcd_batch_apply(ctxs, x, y):
 
 def mcd_batch_lanczos_ground(ctxs, max_iter: int, tol: float, seed: int, dtype: int, psi=None,
                              allow_not_converged: bool = False):
-    """Lanczos ground states of all contexts in lockstep; returns dict with
-    E0, iters, residual (numpy arrays) and status.  psi: None or a list of
+    """Lanczos ground states of all contexts (concurrent per-instance solves,
+    or lockstep launches with MCD_OPT_BATCH_MODE = 1 on ctxs[0]); returns dict
+    with E0, iters, residual (numpy arrays) and status.  psi: None or a list of
     device tensors (or None entries) receiving the normalised Ritz vectors."""
     for c in ctxs:
         c._sync_stream()

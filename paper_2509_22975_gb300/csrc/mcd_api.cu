@@ -86,7 +86,8 @@ namespace {
 // non-blocking CUDA stream that it sets on the instance's context for the
 // call (the context's stream is restored afterwards), so instances run
 // concurrently on the GPU.  Returns the status of the first failing instance
-// (lowest index), its message in ctxs[0]'s last error.
+// (lowest index; an error before a mere MCD_E_NOT_CONVERGED), its message in
+// ctxs[0]'s last error.
 template <typename F>
 int run_instances(mcd_ctx* const* ctxs, int n, F f) {
   const int hw = int(std::thread::hardware_concurrency());
@@ -97,7 +98,8 @@ int run_instances(mcd_ctx* const* ctxs, int n, F f) {
   std::string err_msg;
   auto note = [&](int i, int st, const std::string& msg) {
     std::lock_guard<std::mutex> lock(mu);
-    if (err_idx < 0 || i < err_idx) {
+    const bool soft = st == MCD_E_NOT_CONVERGED, was_soft = err_st == MCD_E_NOT_CONVERGED;
+    if (err_idx < 0 || (was_soft && !soft) || (soft == was_soft && i < err_idx)) {
       err_idx = i;
       err_st = st;
       err_msg = msg;
@@ -272,6 +274,10 @@ int mcd_set_option(mcd_ctx* c, int option, int64_t value) {
     case MCD_OPT_HV_COLS:
       if (value < 0 || value > 2) return fail(c, MCD_E_INVALID, "HV_COLS must be 0, 1 or 2");
       c->hv_cols = int(value);
+      return MCD_OK;
+    case MCD_OPT_BATCH_MODE:
+      if (value < 0 || value > 1) return fail(c, MCD_E_INVALID, "BATCH_MODE must be 0 or 1");
+      c->batch_mode = int(value);
       return MCD_OK;
     case MCD_OPT_BATCH_SPLIT:
       if (value != 0 && value != 1 && value != 2 && value != 4)
@@ -833,6 +839,23 @@ int mcd_batch_apply(mcd_ctx* const* ctxs, int n_inst, const void* x, void* y, in
 
 int mcd_batch_lanczos_ground(mcd_ctx* const* ctxs, int n_inst, int max_iter, double tol, uint64_t seed, int dtype,
                              double* E0, int* iters, double* residual, void* const* psi) {
+  if (ctxs && n_inst > 0 && ctxs[0] && ctxs[0]->batch_mode == 0) {
+    // every instance's own solve, concurrently: each records its E0, steps and
+    // residual; the first failing instance's status (e.g. MCD_E_NOT_CONVERGED)
+    // is returned with every instance's outputs written
+    int st = check_instances(ctxs, n_inst, false);
+    if (st != MCD_OK) return st;
+    if (!E0) return fail(ctxs[0], MCD_E_INVALID, "batch Lanczos arguments");
+    return run_instances(ctxs, n_inst, [&](int i, mcd_ctx* c) {
+      int it = 0;
+      double r = 0.0;
+      const int s = mcd_lanczos_ground(c, max_iter, tol, seed, dtype, E0 + i, psi ? psi[i] : nullptr, &it, &r);
+      if (iters) iters[i] = it;
+      if (residual) residual[i] = r;
+      if (s == MCD_E_NOT_CONVERGED) return fail(c, s, "Lanczos: residual above tol after max_iter steps");
+      return s;
+    });
+  }
   try {
     return batch_lanczos_ground(ctxs, n_inst, max_iter, tol, seed, dtype, E0, iters, residual, psi);
   } catch (const std::bad_alloc&) {

@@ -181,12 +181,14 @@ def test_option_ranges():
           pkg.MCD_OPT_SAMPLER_THREADS: [0, 1, 16], pkg.MCD_OPT_SAMPLER_DEVICE: [0, 1, 2],
           pkg.MCD_OPT_HV_CACHE: [0, 1, 2], pkg.MCD_OPT_HASH_ITEM: [64, 128, 1024, 4096],
           pkg.MCD_OPT_APPLY_SYNC: [0, 1], pkg.MCD_OPT_WAIT_TEST: [-1, 0, 5], pkg.MCD_OPT_KRYLOV_STORE: [0, 1],
-          pkg.MCD_OPT_HV_COLS: [0, 1, 2], pkg.MCD_OPT_BATCH_SPLIT: [0, 1, 2, 4]}
+          pkg.MCD_OPT_HV_COLS: [0, 1, 2], pkg.MCD_OPT_BATCH_SPLIT: [0, 1, 2, 4],
+          pkg.MCD_OPT_BATCH_MODE: [0, 1]}
     bad = {pkg.MCD_OPT_HV_ALGO: [-1, 4], pkg.MCD_OPT_SAMPLER_THREADS: [-1],
            pkg.MCD_OPT_SAMPLER_DEVICE: [-1, 3], pkg.MCD_OPT_HV_CACHE: [-1, 3],
            pkg.MCD_OPT_HASH_ITEM: [0, 32, 63, 100, 8192], pkg.MCD_OPT_APPLY_SYNC: [-1, 2],
            pkg.MCD_OPT_WAIT_TEST: [-2], pkg.MCD_OPT_KRYLOV_STORE: [-1, 2],
-           pkg.MCD_OPT_HV_COLS: [-1, 3], pkg.MCD_OPT_BATCH_SPLIT: [-1, 3, 8], 999: [0]}
+           pkg.MCD_OPT_HV_COLS: [-1, 3], pkg.MCD_OPT_BATCH_SPLIT: [-1, 3, 8],
+           pkg.MCD_OPT_BATCH_MODE: [-1, 2], 999: [0]}
     for opt, vals in ok.items():
         for v in vals:
             ctx.mcd_set_option(opt, v)

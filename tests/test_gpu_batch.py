@@ -82,7 +82,15 @@ def test_batch_apply_equals_single_and_oracle(batch12, dtype, split):
             assert np.all(np.abs(yi.double().cpu().numpy() - ref) <= bound)
 
 
-def test_batch_lanczos_fp64_against_single_and_oracle(batch12):
+@pytest.fixture(params=[pkg.BATCH_POOL, pkg.BATCH_LOCKSTEP], ids=["pool", "lockstep"])
+def mode(request, batch12):
+    # both forms of the batched Lanczos (MCD_OPT_BATCH_MODE, read from the first context)
+    batch12[1][0].mcd_set_option(pkg.MCD_OPT_BATCH_MODE, request.param)
+    yield request.param
+    batch12[1][0].mcd_set_option(pkg.MCD_OPT_BATCH_MODE, pkg.BATCH_POOL)
+
+
+def test_batch_lanczos_fp64_against_single_and_oracle(batch12, mode):
     import scipy.sparse.linalg as sla
     ms, ctxs = batch12
     r = pkg.mcd_batch_lanczos_ground(ctxs, 600, 1e-12, 0, pkg.MCD_F64)
@@ -100,7 +108,7 @@ def test_batch_lanczos_fp64_against_single_and_oracle(batch12):
         assert abs(r["E0"][i] - E_ref) <= 1e-10 * abs(E_ref)
 
 
-def test_batch_lanczos_fp32_and_ritz_vectors(batch12):
+def test_batch_lanczos_fp32_and_ritz_vectors(batch12, mode):
     ms, ctxs = batch12
     sizes = [c.mcd_basis_info(nnz=False)["n_states"] for c in ctxs]
     psi = [torch.empty(n, dtype=torch.float32, device=DEV) for n in sizes]
@@ -118,19 +126,41 @@ def test_batch_lanczos_fp32_and_ritz_vectors(batch12):
 
 @pytest.mark.parametrize("split", [1, 4])
 def test_batch_lanczos_every_work_unit_size(batch12, split):
-    # the fused <v, Hv> partials are summed per work unit: another unit size
-    # sums them in another order, so E0 agrees within rounding
+    # lockstep form: the fused <v, Hv> partials are summed per work unit:
+    # another unit size sums them in another order, so E0 agrees within rounding
     ms, ctxs = batch12
-    ref = pkg.mcd_batch_lanczos_ground(ctxs, 400, 1e-12, 0, pkg.MCD_F64)
-    ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_SPLIT, split)
+    ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_MODE, pkg.BATCH_LOCKSTEP)
     try:
+        ref = pkg.mcd_batch_lanczos_ground(ctxs, 400, 1e-12, 0, pkg.MCD_F64)
+        ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_SPLIT, split)
         r = pkg.mcd_batch_lanczos_ground(ctxs, 400, 1e-12, 0, pkg.MCD_F64)
     finally:
         ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_SPLIT, 0)
+        ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_MODE, pkg.BATCH_POOL)
     assert np.max(np.abs(r["E0"] - ref["E0"]) / np.abs(ref["E0"])) <= 1e-10
 
 
-def test_batch_is_deterministic(batch12):
+def test_batch_stream_pool_equals_separate_solves(batch12):
+    # the default form: every instance's own (cached) solve on a stream pool
+    # gives what separate mcd_lanczos_ground calls give, bit for bit
+    ms, ctxs = batch12
+    sizes = [c.mcd_basis_info(nnz=False)["n_states"] for c in ctxs]
+    psi = [torch.empty(n, dtype=torch.float32, device=DEV) for n in sizes]
+    r = pkg.mcd_batch_lanczos_ground(ctxs, 400, 1e-8, 0, pkg.MCD_F32, psi=psi, allow_not_converged=True)
+    for i, c in enumerate(ctxs):
+        p1 = torch.empty_like(psi[i])
+        s = c.mcd_lanczos_ground(400, 1e-8, 0, pkg.MCD_F32, psi=p1, allow_not_converged=True)
+        assert r["E0"][i] == s["E0"] and r["iters"][i] == s["iters"]
+        assert torch.equal(p1, psi[i])
+    ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_MODE, pkg.BATCH_LOCKSTEP)
+    try:
+        ref = pkg.mcd_batch_lanczos_ground(ctxs, 400, 1e-8, 0, pkg.MCD_F32, allow_not_converged=True)
+    finally:
+        ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_MODE, pkg.BATCH_POOL)
+    assert np.max(np.abs(r["E0"] - ref["E0"])) < 1e-6
+
+
+def test_batch_is_deterministic(batch12, mode):
     ms, ctxs = batch12
     a = pkg.mcd_batch_lanczos_ground(ctxs, 100, 0.0, 4, pkg.MCD_F32)
     b = pkg.mcd_batch_lanczos_ground(ctxs, 100, 0.0, 4, pkg.MCD_F32)
@@ -139,6 +169,7 @@ def test_batch_is_deterministic(batch12):
 
 def test_batch_errors(batch12):
     ms, ctxs = batch12
+    ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_MODE, pkg.BATCH_LOCKSTEP)   # instances of one site count
     from workloads import configs as C
     w = C.rect24_u8()
     big = pkg.Context(0)
@@ -154,6 +185,15 @@ def test_batch_errors(batch12):
     assert e.value.status == -8
     with pytest.raises(pkg.MCDError):
         pkg.mcd_batch_lanczos_ground(ctxs[:2], 0, 1e-10, 0, pkg.MCD_F64)
+    ctxs[0].mcd_set_option(pkg.MCD_OPT_BATCH_MODE, pkg.BATCH_POOL)
+    # the pool form solves instances of any size; a context without a basis
+    # and bad arguments still fail, naming the instance
+    with pytest.raises(pkg.MCDError) as e:
+        pkg.mcd_batch_lanczos_ground([ctxs[0], nob], 50, 1e-10, 0, pkg.MCD_F64)
+    assert e.value.status == -8 and "instance 1" in str(e.value)
+    with pytest.raises(pkg.MCDError) as e:
+        pkg.mcd_batch_lanczos_ground(ctxs[:2], 0, 1e-10, 0, pkg.MCD_F64)
+    assert e.value.status == -1
 
 
 @pytest.mark.slow
