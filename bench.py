@@ -555,9 +555,22 @@ def main():
                     help="lattice of the Lanczos steps (rect24: the 6x4 cluster, for profiling its kernels)")
     ap.add_argument("--green-c5-blocks", type=int, default=40,
                     help="band blocks per excited space of the 6x4 Green function")
+    ap.add_argument("--band-only", type=int, default=0, metavar="N_F",
+                    help="profiling: only the 6x4 band-Lanczos Green function on an N_F-state basis "
+                         "(--green-c5-blocks blocks); prints its record, not the benchmark line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.band_only:
+        import torch
+        import paper_2509_22975_gb300 as pkg
+        from workloads import configs
+        pkg.build()
+        dev = torch.device("cuda", 0)
+        peak, _ = measured_peak()
+        print(json.dumps({"band_green_rect24": band_green(pkg, configs, dev, peak, "rect24_u8", args.band_only,
+                                                          args.green_c5_blocks, mu_half=False)}))
+        return
 
     import numpy as np
     import torch
