@@ -460,7 +460,7 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
   if (bad && !breakdown) return fail(c, MCD_E_BREAKDOWN, "Lanczos: non-finite coefficient");
   int status = MCD_OK;
   if (!done && tol > 0) status = MCD_E_NOT_CONVERGED;
-  if (!psi && !fp32) return status;
+  if (!psi && !fp32 && !c->keep_gs) return status;
 
   // Ritz vector sum_k ev[k] sig_k s_k (change-of-basis Eq. of App. B), in fp64
   // for the fp32 form (whose E0 is then the fp64 Rayleigh quotient of it)
@@ -469,6 +469,19 @@ int run(mcd_ctx* c, int max_iter, double tol, uint64_t seed, double* E0_out, T* 
   // (fp32 vectors: double-float sum, the same steps whether the vectors are
   // stored or regenerated, so both give the same bits)
   double* p64 = fp32 ? w.psi64 : reinterpret_cast<double*>(psi);
+  if (!p64) {
+    // fp64 without a caller's vector (the ground state is only kept): the Ritz
+    // vector is formed in the kept copy itself and normalised in place below
+    if (!c->gs_psi || c->gs_n != n) {
+      if (c->gs_psi) cudaFreeAsync(c->gs_psi, s);
+      c->gs_psi = nullptr;
+      c->gs_valid = false;
+      e = cudaMallocAsync(&c->gs_psi, sizeof(double) * n, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "ground-state copy");
+      c->gs_n = n;
+    }
+    p64 = c->gs_psi;
+  }
   std::vector<float2> coef32(fp32 ? m : 0);
   for (size_t k = 0; k < coef32.size(); ++k) coef32[k] = split_coef(coef[k]);
   if (w.stored) {

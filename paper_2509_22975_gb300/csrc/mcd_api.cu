@@ -849,7 +849,9 @@ int mcd_batch_lanczos_ground(mcd_ctx* const* ctxs, int n_inst, int max_iter, dou
     return run_instances(ctxs, n_inst, [&](int i, mcd_ctx* c) {
       int it = 0;
       double r = 0.0;
+      c->keep_gs = true;   // as the lockstep form, every instance keeps its ground state
       const int s = mcd_lanczos_ground(c, max_iter, tol, seed, dtype, E0 + i, psi ? psi[i] : nullptr, &it, &r);
+      c->keep_gs = false;
       if (iters) iters[i] = it;
       if (residual) residual[i] = r;
       if (s == MCD_E_NOT_CONVERGED) return fail(c, s, "Lanczos: residual above tol after max_iter steps");

@@ -238,6 +238,8 @@ struct mcd_ctx {
   int hv_cols = 0;                      // many-column kernel: 0 timed pick, 1 pipelined tiles, 2 CTA per item
   int batch_split = 0;                  // batched H*v: parts per work item (0 timed, 1, 2 or 4)
   int batch_mode = 0;                   // batched Lanczos: 0 per-instance solves on a stream pool, 1 lockstep launches
+  bool keep_gs = false;                 // Lanczos forms the Ritz vector (kept for the Green function) even
+                                        // without a caller's psi (set by the batched solves)
   int cols_pick[65][2] = {};            // timed pick per column count (<= 64) and dtype: 0 none, 1 tiles, 2 items
   cudaEvent_t tune_ev[3] = {nullptr, nullptr, nullptr};
   int64_t wait_test_item = -1;          // one-shot: withhold this item's copies (time-out test)
