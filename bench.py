@@ -202,7 +202,32 @@ def cpu_baseline(seconds: float = 10.0, n_states: int = 1 << 17) -> dict:
                                    "sample": f"oracle H~x repeated for {t6:.1f} s on an oracle-sampled "
                                              f"{len(B6)}-state MC basis of the 6x4 t-t' lattice (11+11 electrons)"}
     out["variants"] = variants
+    # the oracle's Lanczos (App. B, its matrix-free H~x each step) for 5
+    # iterations on the 4x4 sample; the caller extrapolates per iteration to
+    # the workload's nonzeros
+    from oracle import lanczos as OL
+    t0 = time.perf_counter()
+    OL.lanczos(lambda v: oracle_apply(B, M, v)[1], len(B), max_iter=5, tol=0.0, seed=0)
+    out["lanczos_sample"] = {"iterations": 5, "s_per_iter": (time.perf_counter() - t0) / 5, "nnz": nnz,
+                             "n_states": len(B)}
+    out["host_cpu"] = host_cpu_name()
     return out
+
+
+def host_cpu_name() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm part
+    number), with the machine type and core count."""
+    import platform
+    name = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and not name:
+                    name = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return f"{platform.machine()} {name} x{os.cpu_count()}".strip()
 
 
 def run_reference(args):
@@ -766,7 +791,12 @@ def main():
         out["fp32_speedup_vs_plain_fp64"] = out["lanczos_iters_per_s_fp32"] / out["lanczos_iters_per_s_fp64_plain"]
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline()
+        cb = cpu_baseline()
+        ls = cb["lanczos_sample"]
+        # one oracle Lanczos iteration on this workload, extrapolated by its nonzeros
+        cb["lanczos_s_per_iter_extrapolated"] = ls["s_per_iter"] * nnz / ls["nnz"]
+        cb["lanczos_iters_per_s_extrapolated"] = 1.0 / cb["lanczos_s_per_iter_extrapolated"]
+        out["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(out))
     if dist:
