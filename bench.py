@@ -429,7 +429,23 @@ def cache_build_ms(pkg, ctx, n, dev):
     return ev[0].elapsed_time(ev[1]) - ev[1].elapsed_time(ev[2])
 
 
-def rect24_hv(pkg, configs, dev, peak, cols=(1, 24, 48), reps=5):
+def median_apply_ms(ctx, x, y, reps=20):
+    """Median of reps back-to-back applications, each bracketed by its own
+    CUDA event pair on the launching stream (after 3 untimed ones)."""
+    import torch
+    for _ in range(3):
+        ctx.mcd_apply(x, y)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    ev[0].record()
+    for i in range(reps):
+        ctx.mcd_apply(x, y)
+        ev[i + 1].record()
+    torch.cuda.synchronize()
+    return statistics.median(ev[i].elapsed_time(ev[i + 1]) for i in range(reps))
+
+
+def rect24_hv(pkg, configs, dev, peak, cols=(1, 24, 48)):
     """H~V on the 6x4 t-t' cluster (24 sites, 11 + 11 electrons, Monte Carlo
     basis of 5e7 states), fp32, each width timed alone with CUDA events after
     warm-up; X and Y are far larger than L2.  The first H~v builds the
@@ -452,16 +468,7 @@ def rect24_hv(pkg, configs, dev, peak, cols=(1, 24, 48), reps=5):
     for L_ in cols:
         x = torch.randn(n, L_, dtype=torch.float32, device=dev)
         y = torch.empty_like(x)
-        for _ in range(3):
-            ctx.mcd_apply(x, y)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            ctx.mcd_apply(x, y)
-        e1.record()
-        torch.cuda.synchronize()
-        t_ms = e0.elapsed_time(e1) / reps
+        t_ms = median_apply_ms(ctx, x, y)
         bytes_ = n * (8 + 2 * L_ * 4)
         res[f"L{L_}"] = {"ms": t_ms, "Gconn_per_s": nnz * L_ / (t_ms * 1e-3) / 1e9,
                          "algorithmic_GBps": bytes_ / (t_ms * 1e-3) / 1e9,
@@ -742,17 +749,7 @@ def main():
         for L_ in args.hv_cols:
             x = torch.randn(n, L_, dtype=torch.float32, device=dev)
             y = torch.empty_like(x)
-            for _ in range(3):
-                ctx.mcd_apply(x, y)
-            torch.cuda.synchronize()
-            reps = 10
-            h0e, h1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            h0e.record()
-            for _ in range(reps):
-                ctx.mcd_apply(x, y)
-            h1e.record()
-            torch.cuda.synchronize()
-            t_ms = h0e.elapsed_time(h1e) / reps
+            t_ms = median_apply_ms(ctx, x, y)
             bytes_ = n * (8 + 2 * L_ * 4)
             hv[f"L{L_}"] = {"ms": t_ms, "Gconn_per_s": nnz * L_ / (t_ms * 1e-3) / 1e9,
                             "algorithmic_GBps": bytes_ / (t_ms * 1e-3) / 1e9,
