@@ -356,7 +356,8 @@ __device__ __forceinline__ void consume_item(const CArgs& a, const HamParams& hp
                                              const uint32_t* colp, const unsigned char* recp, const uint16_t* mapp,
                                              const T* xs, const uint64_t* wp, const uint32_t* pp, const T* ybp,
                                              const double* c64, const float* chi, const float* clo,
-                                             const float* dhi, const float* dlo, const double* d64, T& dh, T& dl) {
+                                             const float* dhi, const float* dlo, const double* d64, T& dh, T& dl,
+                                             int rot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t half = a.n_sites >= 32 ? 0xFFFFFFFFu : ((1u << a.n_sites) - 1u);
   const int nsl = int((it.hi - it.lo + 31) / 32);
@@ -364,7 +365,15 @@ __device__ __forceinline__ void consume_item(const CArgs& a, const HamParams& hp
   const bool wide = (it.flags & 1u) != 0u;
   T* __restrict__ y = static_cast<T*>(a.y);
   T* __restrict__ yb = static_cast<T*>(a.yb);
-  for (int sl = warp; sl < nsl; sl += SCfg<T>::kCons) {
+  // Slices, longest first (the states are sorted by record count), go to the
+  // consumer warps in serpentine order: pass p of kCons slices runs forwards
+  // for even p and backwards for odd p, so the warps that take a second slice
+  // are those with the shortest first one; the order is rotated by rot, which
+  // changes from item to item, so that the extra slices fall on other warps.
+  const int wpos = (warp + SCfg<T>::kCons - rot) % SCfg<T>::kCons;
+  for (int pass = 0;; ++pass) {
+    const int sl = pass * SCfg<T>::kCons + ((pass & 1) ? SCfg<T>::kCons - 1 - wpos : wpos);
+    if (sl >= nsl) break;
     const uint16_t loc = mapp[sl * 32 + lane];
     if (loc == kNoState) continue;
     const uint32_t k = it.lo + loc;
@@ -562,6 +571,7 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
     // consumers
     for (int64_t i = 0; i < n_my; ++i) {
       const int st = int(i % kSStages);
+      const int rot = int((i * 4) % SCfg<T>::kCons);
       if (!mbar_wait(&s_full[st], uint32_t((i / kSStages) & 1), a.spin_limit)) {
         failed = true;
         break;
@@ -576,7 +586,7 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
                                      reinterpret_cast<const uint64_t*>(stage + kSOffAux) + s_aoff[st],
                                      reinterpret_cast<const uint32_t*>(stage + kSOffAux) + s_aoff[st],
                                      reinterpret_cast<const T*>(stage + kSOffAux2) + s_boff[st], s_c64, s_chi,
-                                     s_clo, s_dhi, s_dlo, s_d64, dh, dl);
+                                     s_clo, s_dhi, s_dlo, s_d64, dh, dl, rot);
       } else if (s_direct[st] == 2) {   // all but the x rows in the stage
         const uint32_t* colp = reinterpret_cast<const uint32_t*>(stage + kSOffCol) + s_coff[st];
         consume_item<T, PASS_A, DOT>(a, hp, it, s_sb[st], colp, stage,
@@ -584,12 +594,12 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
                                      reinterpret_cast<const uint64_t*>(stage + kSOffAux) + s_aoff[st],
                                      reinterpret_cast<const uint32_t*>(stage + kSOffAux) + s_aoff[st],
                                      reinterpret_cast<const T*>(stage + kSOffAux2) + s_boff[st], s_c64, s_chi,
-                                     s_clo, s_dhi, s_dlo, s_d64, dh, dl);
+                                     s_clo, s_dhi, s_dlo, s_d64, dh, dl, rot);
       } else {                   // records too large for the stage: global memory
         const uint32_t sb = s_sb[st];
         consume_item<T, PASS_A, DOT>(a, hp, it, sb, a.col + it.slice0, recg + int64_t(it.g0) * kGroup,
                                      a.smap + int64_t(it.slice0) * 32, xg + sb, a.words + it.lo, a.perm + it.lo,
-                                     yb + it.lo, s_c64, s_chi, s_clo, s_dhi, s_dlo, s_d64, dh, dl);
+                                     yb + it.lo, s_c64, s_chi, s_clo, s_dhi, s_dlo, s_d64, dh, dl, rot);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&s_empty[st]);
