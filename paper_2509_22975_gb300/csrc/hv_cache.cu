@@ -372,7 +372,7 @@ __device__ __forceinline__ void consume_item(const CArgs& a, const HamParams& hp
   // changes from item to item, so that the extra slices fall on other warps.
   const int wpos = (warp + SCfg<T>::kCons - rot) % SCfg<T>::kCons;
   for (int pass = 0;; ++pass) {
-    const int sl = pass * SCfg<T>::kCons + ((pass & 1) ? SCfg<T>::kCons - 1 - wpos : wpos);
+    const int sl = serp_slice(pass, wpos, SCfg<T>::kCons);
     if (sl >= nsl) break;
     const uint16_t loc = mapp[sl * 32 + lane];
     if (loc == kNoState) continue;

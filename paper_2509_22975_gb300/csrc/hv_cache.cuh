@@ -94,6 +94,14 @@ struct CArgs {
 
 // ---- apply --------------------------------------------------------------------------
 
+// Slice of a work item for the consumer warp at position wpos of nw, on its
+// pass `pass` over the item: an item's slices are sorted longest first, and
+// the passes run forwards and backwards in turn (serpentine), so the warps
+// that take a further slice are those whose previous one was shortest.
+__device__ __forceinline__ int serp_slice(int pass, int wpos, int nw) {
+  return pass * nw + ((pass & 1) ? nw - 1 - wpos : wpos);
+}
+
 __device__ __forceinline__ float flip_sign(float x, uint32_t sg) { return __int_as_float(__float_as_int(x) ^ int(sg)); }
 __device__ __forceinline__ double flip_sign(double x, uint32_t sg) {
   return __longlong_as_double(__double_as_longlong(x) ^ (static_cast<long long>(sg) << 32));

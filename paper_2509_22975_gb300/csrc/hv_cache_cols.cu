@@ -370,7 +370,11 @@ __global__ void __launch_bounds__(kTThreads, 2) hv_tile_kernel(const CArgs a, co
         const unsigned char* recb = m.rdirect ? recg + int64_t(it.g0) * kGroup : stage;
         const int nsl = int((it.hi - it.lo + 31) / 32);
         const bool wide = (it.flags & 1u) != 0u;
-        for (int sl = warp; sl < nsl; sl += kTCons) {
+        // serpentine slice order, rotated from item to item (see serp_slice)
+        const int wpos = (warp + kTCons - int((ri * 4) % kTCons)) % kTCons;
+        for (int pass = 0;; ++pass) {
+          const int sl = serp_slice(pass, wpos, kTCons);
+          if (sl >= nsl) break;
           const uint32_t ga = colp[sl], gz = colp[sl + 1];
           const uint32_t locs = mapp[sl * 32 + lane];
           for (int t0 = 0; t0 < 32; t0 += spw) {

@@ -80,7 +80,9 @@ __global__ void __launch_bounds__(kCT) hv_item_kernel(const CArgs a, const HamPa
       }
     };
     const int nsl = int((it.hi - it.lo + 31) / 32);
-    for (int sl = warp; sl < nsl; sl += kCWarps) {
+    for (int pass = 0;; ++pass) {   // serpentine slice order (see serp_slice)
+      const int sl = serp_slice(pass, warp, kCWarps);
+      if (sl >= nsl) break;
       const int64_t s = int64_t(it.slice0) + sl;
       const uint32_t ga = __ldg(a.col + s), gz = __ldg(a.col + s + 1);
       const uint32_t locs = __ldg(a.smap + s * 32 + lane);   // the slice's lane map, one load per warp
