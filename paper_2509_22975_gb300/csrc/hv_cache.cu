@@ -461,6 +461,7 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
   __shared__ __align__(8) uint64_t s_full[kSStages], s_empty[kSStages];
   __shared__ int s_direct[kSStages], s_xoff[kSStages], s_coff[kSStages], s_aoff[kSStages], s_boff[kSStages];
   __shared__ CItem s_item[kSStages];
+  __shared__ int64_t s_idx[kSStages];   // work item in each stage (-1: no more items)
   __shared__ uint32_t s_sb[kSStages];
   __shared__ float s_dhi[kMaxSites + 1], s_dlo[kMaxSites + 1];
   __shared__ double s_d64[kMaxSites + 1];
@@ -487,28 +488,48 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t n_my = blockIdx.x < a.n_items ? (a.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const T* __restrict__ xg = static_cast<const T*>(PASS_A ? a.x : a.xb);   // rows in layout order
+  T dh = T(0), dl = T(0);   // this thread's part of <x, y> (consumers)
   const T* __restrict__ yb = static_cast<const T*>(a.yb);                    // pass B's part of y
   const unsigned char* recg = static_cast<const unsigned char*>(a.rec);
-  T dh = T(0), dl = T(0);   // this thread's part of <x, y> (consumers)
   bool failed = false;
   int64_t issued[kSStages];   // producer: last item index issued into each stage (-1 none)
   for (int s = 0; s < kSStages; ++s) issued[s] = -1;
 
   if (warp == SCfg<T>::kCons) {
-    // producer: one thread issues the copies of the CTA's items, in order
+    // producer: one thread takes the CTA's work items (one ahead: the next
+    // item's descriptor loads while this one is issued) and issues their
+    // copies; past the last item it hands the consumers an end marker.  With
+    // <x, y> the items are blockIdx.x + i gridDim.x (the CTA partials then have
+    // a fixed order); without, they are claimed from the launch's counter, so
+    // CTAs that drew short items take more of them.
     if (lane == 0) {
-      CItem nxt;   // descriptor of the next item, loaded while the current one is issued
-      if (n_my > 0) nxt = a.items[blockIdx.x];
-      for (int64_t i = 0; i < n_my; ++i) {
+      int64_t claims = 0;
+      auto claim = [&]() -> int64_t {
+        if constexpr (DOT) return int64_t(blockIdx.x) + (claims++) * int64_t(gridDim.x);
+        return int64_t(atomicAdd(a.sched, 1u));
+      };
+      CItem nxt{};
+      int64_t idx_next = claim();
+      if (idx_next < a.n_items) nxt = a.items[idx_next];
+      for (int64_t i = 0;; ++i) {
         const int st = int(i % kSStages);
         const CItem it = nxt;
-        if (i + 1 < n_my) nxt = a.items[blockIdx.x + (i + 1) * gridDim.x];
+        const int64_t idx = idx_next;
+        if (idx < a.n_items) {
+          idx_next = claim();
+          if (idx_next < a.n_items) nxt = a.items[idx_next];
+        }
         if (!mbar_wait(&s_empty[st], uint32_t((i / kSStages) & 1) ^ 1u, a.spin_limit)) {
           failed = true;
           break;
         }
+        if (idx >= a.n_items) {
+          s_idx[st] = -1;
+          mbar_arrive(&s_full[st]);
+          break;
+        }
+        s_idx[st] = idx;
         const uint32_t sb = it.sb, se = it.se;
         const int nsl = int((it.hi - it.lo + 31) / 32);
         const uint32_t g0 = it.g0, g1 = it.g1;
@@ -543,7 +564,7 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
         const uint32_t bytes = direct ? 0u
                                       : rb + mb + uint32_t(chi - clo) + (x_out ? 0u : uint32_t(xhi - xlo)) +
                                             uint32_t(ahi - alo) + uint32_t(bhi - blo);
-        if (blockIdx.x + i * int64_t(gridDim.x) == a.withhold) {
+        if (idx == a.withhold) {
           // time-out test: no arrival and no copy for this item, so the
           // waits on its stage run out (nothing is in flight for it)
         } else if (bytes == 0u) {
@@ -568,14 +589,16 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
       }
     }
   } else {
-    // consumers
-    for (int64_t i = 0; i < n_my; ++i) {
+    // consumers: the items of the stages in turn until the end marker
+    for (int64_t i = 0;; ++i) {
       const int st = int(i % kSStages);
-      const int rot = int((i * 4) % SCfg<T>::kCons);
       if (!mbar_wait(&s_full[st], uint32_t((i / kSStages) & 1), a.spin_limit)) {
         failed = true;
         break;
       }
+      const int64_t idx = s_idx[st];
+      if (idx < 0) break;
+      const int rot = int((idx * 4) % SCfg<T>::kCons);
       const CItem it = s_item[st];
       const unsigned char* stage = s_dyn + st * kSStageBytes;
       if (s_direct[st] == 0) {   // every array of the item in the stage: shared-memory loads
@@ -615,7 +638,18 @@ __global__ void __launch_bounds__(SCfg<T>::kThreads, 2) hv_stream_kernel(const C
     if (threadIdx.x == 0) atomicOr(a.err, 1u);
     __syncthreads();
   }
-  if constexpr (DOT) dot_reduce<SCfg<T>::kCons + 1>(a, double(dh) + double(dl), s_red);
+  if constexpr (DOT) {
+    dot_reduce<SCfg<T>::kCons + 1>(a, double(dh) + double(dl), s_red);
+  } else {
+    // the last CTA to finish resets the item counter for the next launch
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) s_last = atomicAdd(a.sched + 1, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+      a.sched[0] = 0u;
+      a.sched[1] = 0u;
+    }
+  }
 }
 
 // x in the layout's order: xb[k] = x[perm[k]] (one column), four positions per
@@ -743,6 +777,8 @@ int build_layout(mcd_ctx* c, Layout& L, const LayoutItems& li, const std::vector
     if (e == cudaSuccess) e = cudaMemcpyAsync(cc.clo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, s);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(cc.err, 0, 4, s);
+  if (e == cudaSuccess && !cc.sched) e = cudaMallocAsync(reinterpret_cast<void**>(&cc.sched), 16, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cc.sched, 0, 16, s);
   if (e == cudaSuccess) e = cudaMallocAsync(&d_bcls, std::max<size_t>(bcls.size(), 1) * 2, s);
   if (e == cudaSuccess && !bcls.empty())
     e = cudaMemcpyAsync(d_bcls, bcls.data(), bcls.size() * 2, cudaMemcpyHostToDevice, s);
@@ -920,6 +956,7 @@ cudaError_t launch_stream(mcd_ctx* c, const void* x, void* y, double* partials, 
     a.dot_partials = partials;
     a.ticket = ticket;
     a.dot_out = dot_out;
+    a.sched = L.cc.sched;
     int64_t grid = std::min<int64_t>(a.n_items, ctas);
     if (dot) grid = std::min<int64_t>(grid, max_parts);
     if (grid <= 0) {
@@ -973,6 +1010,7 @@ void free_cache(Layout& L, cudaStream_t s) {
   ConnCache& cc = L.cc;
   auto f = [s](void* p) { if (p) cudaFreeAsync(p, s); };
   f(cc.items); f(cc.col); f(cc.smap); f(cc.rec); f(cc.c64); f(cc.xb); f(cc.yb); f(cc.xbm); f(cc.units);
+  f(cc.sched);
   cc = ConnCache();
 }
 

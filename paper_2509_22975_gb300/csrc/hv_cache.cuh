@@ -84,6 +84,7 @@ struct CArgs {
   int64_t n_units;
   uint32_t spin_limit;           // polls of an mbarrier before a wait gives up
   int64_t withhold;              // time-out test: item whose copies are not issued (-1 none)
+  unsigned int* sched;           // streaming kernel: [0] next work item to claim, [1] CTAs done (both 0 between launches)
   // build
   const uint16_t* bond_cls;      // [n_bonds] record class of each bond
   uint16_t* cnt;                 // [n] records of each state

@@ -131,6 +131,7 @@ struct ConnCache {
   void* xbm = nullptr;           // X (many columns) in this layout's order (pass B)
   void* yb = nullptr;            // pass B's part of y (streaming kernels), read by pass A
   unsigned int* err = nullptr;   // set by a kernel whose bounded wait ran out
+  unsigned int* sched = nullptr; // streaming kernel's item counter and CTA ticket (zero between launches)
   int64_t items_cap = 0, col_cap = 0, smap_cap = 0, rec_cap = 0, cls_cap = 0, xb_cap = 0, yb_cap = 0, xbm_cap = 0;
   // many-column kernel: work units (items of one stage range, column tile)
   // of the last column count and element size (the items' stage ranges are
