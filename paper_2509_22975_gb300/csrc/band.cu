@@ -364,10 +364,8 @@ __global__ void reduce_partials_kernel(const double* partials, int nparts, int n
   out[pr] = s;
 }
 
-// fp32 vectors: the same combination with the fp64 coefficients given as
-// float pairs (hi, lo) (CH / CL, same layout as C1 | C2, beta as bh + bl):
-// each product x c = x ch + x cl is formed exactly as float terms and summed
-// into a double-float (hi, lo), rounded once to float at the end.
+// (hi, lo) += x (ch + cl) in double-float: the product x ch split exactly by
+// an FMA, x cl added to its error term, then Knuth's two-sum
 __device__ __forceinline__ void df_add(float& hi, float& lo, float x, float ch, float cl) {
   const float p = x * ch;
   const float e = fmaf(x, ch, -p) + x * cl;
@@ -376,20 +374,6 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x, float ch, 
   hi = sum;
 }
 
-__global__ void block_combine32_kernel(const float* W, float* out, int pw, float bh, float bl, const float* X1,
-                                       int p1, const float* CH1, const float* CL1, const float* X2, int p2,
-                                       const float* CH2, const float* CL2, int ld, int64_t n) {
-  const int64_t total = n * pw;
-  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t r = e / pw;
-    const int j = int(e - r * pw);
-    float hi = 0.f, lo = 0.f;
-    if (bh != 0.f || bl != 0.f) df_add(hi, lo, W[r * ld + j], bh, bl);
-    for (int i = 0; i < p1; ++i) df_add(hi, lo, X1[r * ld + i], __ldg(CH1 + i * pw + j), __ldg(CL1 + i * pw + j));
-    for (int i = 0; i < p2; ++i) df_add(hi, lo, X2[r * ld + i], __ldg(CH2 + i * pw + j), __ldg(CL2 + i * pw + j));
-    out[r * ld + j] = hi + lo;
-  }
-}
 
 // fp32 vectors, K = p1 + p2 <= 64 and pw <= 32: the same combination on the
 // tensor cores with exact integer sums.  Each row r of [X1 X2] is scaled by a
@@ -776,50 +760,40 @@ class BandLanczos {
   }
 
   // host G = [X1[:, :pa1] X2[:, :pa2]]^T Y[:, :pb] ((pa1 + pa2) x pb, X1's
-  // rows first): one pass over the rows in fp32 when pa1 + pa2 <= 64
+  // rows first): one pass over the rows in fp32 (pa1 + pa2 <= 2 kMaxSites =
+  // 64), one product at a time in fp64
   int gram2(const T* X1, int pa1, const T* X2, int pa2, const T* Y, int pb, std::vector<double>& G) {
     cudaStream_t s = c_->stream;
     const int pa = pa1 + pa2;
+    int npair = pa * pb;
     if constexpr (sizeof(T) == 4) {
-      if (pa <= kMaxOrb) {
-        const size_t smem = GramSmem(pa, pb, L_, Y == X1 && pb == pa1, pa2 > 0).bytes();
-        if (smem > 48 * 1024) {
-          const cudaError_t ea =
-              cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-          if (ea != cudaSuccess) return cuda_fail(c_, ea, "Gram kernel shared memory");
-        }
-        gram_tc_kernel<<<nparts_, kThreads, smem, s>>>(X1, pa1, pa2 ? X2 : nullptr, pa2, Y, pb, L_, n_, part_);
-        MCD_LAUNCHED(c_);
-        reduce_partials_kernel<<<(pa * pb + 255) / 256, 256, 0, s>>>(part_, nparts_, pa * pb, gram_);
-        MCD_LAUNCHED(c_);
-        G.resize(size_t(pa) * pb);
-        cudaError_t e = cudaMemcpyAsync(G.data(), gram_, sizeof(double) * pa * pb, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        return e == cudaSuccess ? MCD_OK : cuda_fail(c_, e, "Gram");
+      if (pa > kMaxOrb) return fail(c_, MCD_E_INVALID, "band Lanczos: Gram of more than 64 columns");
+      const size_t smem = GramSmem(pa, pb, L_, Y == X1 && pb == pa1, pa2 > 0).bytes();
+      if (smem > 48 * 1024) {
+        const cudaError_t ea =
+            cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (ea != cudaSuccess) return cuda_fail(c_, ea, "Gram kernel shared memory");
       }
-    }
-    // one product at a time (fp64 vectors, or more than 64 rows)
-    std::vector<double> G1, G2;
-    if constexpr (sizeof(T) == 8) {
-      gram_kernel<T><<<nparts_, kThreads, 0, s>>>(X1, pa1, Y, pb, L_, n_, part_);
-      MCD_LAUNCHED(c_);
-      reduce_partials_kernel<<<(pa1 * pb + 255) / 256, 256, 0, s>>>(part_, nparts_, pa1 * pb, gram_);
-      MCD_LAUNCHED(c_);
-      G1.resize(size_t(pa1) * pb);
-      cudaError_t e = cudaMemcpyAsync(G1.data(), gram_, sizeof(double) * pa1 * pb, cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) return cuda_fail(c_, e, "Gram");
+      gram_tc_kernel<<<nparts_, kThreads, smem, s>>>(X1, pa1, pa2 ? X2 : nullptr, pa2, Y, pb, L_, n_, part_);
     } else {
-      const int st = gram2(X1, pa1, nullptr, 0, Y, pb, G1);
-      if (st) return st;
+      if (pa2) {   // X2's rows after X1's
+        std::vector<double> G1, G2;
+        int st = gram2(X1, pa1, nullptr, 0, Y, pb, G1);
+        if (st == MCD_OK) st = gram2(X2, pa2, nullptr, 0, Y, pb, G2);
+        if (st != MCD_OK) return st;
+        G = G1;
+        G.insert(G.end(), G2.begin(), G2.end());
+        return MCD_OK;
+      }
+      gram_kernel<T><<<nparts_, kThreads, 0, s>>>(X1, pa1, Y, pb, L_, n_, part_);
     }
-    if (pa2) {
-      const int st = gram2(X2, pa2, nullptr, 0, Y, pb, G2);
-      if (st) return st;
-    }
-    G = G1;
-    G.insert(G.end(), G2.begin(), G2.end());
-    return MCD_OK;
+    MCD_LAUNCHED(c_);
+    reduce_partials_kernel<<<(npair + 255) / 256, 256, 0, s>>>(part_, nparts_, npair, gram_);
+    MCD_LAUNCHED(c_);
+    G.resize(size_t(npair));
+    cudaError_t e = cudaMemcpyAsync(G.data(), gram_, sizeof(double) * npair, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? MCD_OK : cuda_fail(c_, e, "Gram");
   }
 
   // out = beta W + X1 C1 + X2 C2 (C1: p1 x pw, C2: p2 x pw)
@@ -831,78 +805,65 @@ class BandLanczos {
     if (p2) std::copy(C2.begin(), C2.begin() + size_t(p2) * pw, buf.begin() + size_t(kMaxOrb) * kMaxOrb);
     cudaError_t e;
     if constexpr (sizeof(T) == 4) {
-      // float pairs (hi, lo) of every coefficient: [hi C1 | hi C2 | lo C1 | lo C2]
       const size_t m = size_t(kMaxOrb) * kMaxOrb;
-      std::vector<float> f(4 * m);
-      for (size_t i = 0; i < 2 * m; ++i) {
-        const float h = float(buf[i]);
-        f[i] = h;
-        f[2 * m + i] = float(buf[i] - double(h));
-      }
       const float bh = float(beta), bl = float(beta - double(bh));
       const int K = p1 + p2;
-      if (K <= kCK && pw <= kCN) {
-        // integer slices of the coefficients of [C1; C2] per column (see block_combine_tc_kernel)
-        const int KS = (K + 15) / 16, NT = (pw + 7) / 8;
-        std::vector<uint16_t> sl(size_t(4) * NT * 8 * kCW * 2, 0);
-        std::vector<int> fe(size_t(NT) * 8, 0);
-        for (int j = 0; j < pw; ++j) {
-          double mx = 0.0;
-          for (int k = 0; k < K; ++k)
-            mx = std::max(mx, std::fabs(k < p1 ? buf[size_t(k) * pw + j] : buf[m + size_t(k - p1) * pw + j]));
-          if (!(mx >= 0x1p-119)) continue;   // a zero column (or one below 2^-119): slices stay zero
-          int ex = 0;
-          std::frexp(mx, &ex);                // mx in [2^(ex-1), 2^ex)
-          fe[j] = ex;
-          for (int k = 0; k < K; ++k) {
-            double v = std::ldexp(k < p1 ? buf[size_t(k) * pw + j] : buf[m + size_t(k - p1) * pw + j], 8 - ex);
-            for (int i = 0; i < 4; ++i) {
-              const double qi = std::nearbyint(v);
-              v = (v - qi) * 256.0;
-              // |qi| <= 256: exact in bf16 (sign, exponent, 7 stored bits)
-              const float fq = float(qi);
-              uint32_t bits;
-              std::memcpy(&bits, &fq, 4);
-              sl[(size_t(i) * NT * 8 + j) * kCW * 2 + k] = uint16_t(bits >> 16);
-            }
+      // orbitals share one spin, so a block has at most kMaxSites = 32 columns:
+      // K <= 64 and pw <= 32 always hold
+      if (K > kCK || pw > kCN) return fail(c_, MCD_E_INVALID, "band Lanczos: block wider than 32 columns");
+      // integer slices of the coefficients of [C1; C2] per column (see block_combine_tc_kernel)
+      const int KS = (K + 15) / 16, NT = (pw + 7) / 8;
+      std::vector<uint16_t> sl(size_t(4) * NT * 8 * kCW * 2, 0);
+      std::vector<int> fe(size_t(NT) * 8, 0);
+      for (int j = 0; j < pw; ++j) {
+        double mx = 0.0;
+        for (int k = 0; k < K; ++k)
+          mx = std::max(mx, std::fabs(k < p1 ? buf[size_t(k) * pw + j] : buf[m + size_t(k - p1) * pw + j]));
+        if (!(mx >= 0x1p-119)) continue;   // a zero column (or one below 2^-119): slices stay zero
+        int ex = 0;
+        std::frexp(mx, &ex);                // mx in [2^(ex-1), 2^ex)
+        fe[j] = ex;
+        for (int k = 0; k < K; ++k) {
+          double v = std::ldexp(k < p1 ? buf[size_t(k) * pw + j] : buf[m + size_t(k - p1) * pw + j], 8 - ex);
+          for (int i = 0; i < 4; ++i) {
+            const double qi = std::nearbyint(v);
+            v = (v - qi) * 256.0;
+            // |qi| <= 256: exact in bf16 (sign, exponent, 7 stored bits)
+            const float fq = float(qi);
+            uint32_t bits;
+            std::memcpy(&bits, &fq, 4);
+            sl[(size_t(i) * NT * 8 + j) * kCW * 2 + k] = uint16_t(bits >> 16);
           }
         }
-        uint32_t* dsl = reinterpret_cast<uint32_t*>(coef_);
-        int* dfe = reinterpret_cast<int*>(dsl + size_t(4) * NT * 8 * kCW);
-        e = cudaMemcpyAsync(dsl, sl.data(), sl.size() * 2, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dfe, fe.data(), fe.size() * 4, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
-        const int grid = int(std::max<int64_t>(1, std::min<int64_t>((n_ + 127) / 128, int64_t(device_sms()) * 8)));
-        const float* x2 = X2 ? X2 : X1;
+      }
+      uint32_t* dsl = reinterpret_cast<uint32_t*>(coef_);
+      int* dfe = reinterpret_cast<int*>(dsl + size_t(4) * NT * 8 * kCW);
+      e = cudaMemcpyAsync(dsl, sl.data(), sl.size() * 2, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dfe, fe.data(), fe.size() * 4, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
+      const int grid = int(std::max<int64_t>(1, std::min<int64_t>((n_ + 127) / 128, int64_t(device_sms()) * 8)));
+      const float* x2 = X2 ? X2 : X1;
 #define MCD_COMBINE_TC(ks, nt)                                                                              \
   block_combine_tc_kernel<ks, nt><<<grid, kThreads, 0, s>>>(W, out, pw, bh, bl, X1, p1, x2, p2, dsl, dfe, L_, n_)
-        switch (KS * 8 + NT) {
-          case 9: MCD_COMBINE_TC(1, 1); break;
-          case 10: MCD_COMBINE_TC(1, 2); break;
-          case 11: MCD_COMBINE_TC(1, 3); break;
-          case 12: MCD_COMBINE_TC(1, 4); break;
-          case 17: MCD_COMBINE_TC(2, 1); break;
-          case 18: MCD_COMBINE_TC(2, 2); break;
-          case 19: MCD_COMBINE_TC(2, 3); break;
-          case 20: MCD_COMBINE_TC(2, 4); break;
-          case 25: MCD_COMBINE_TC(3, 1); break;
-          case 26: MCD_COMBINE_TC(3, 2); break;
-          case 27: MCD_COMBINE_TC(3, 3); break;
-          case 28: MCD_COMBINE_TC(3, 4); break;
-          case 33: MCD_COMBINE_TC(4, 1); break;
-          case 34: MCD_COMBINE_TC(4, 2); break;
-          case 35: MCD_COMBINE_TC(4, 3); break;
-          default: MCD_COMBINE_TC(4, 4); break;
-        }
-#undef MCD_COMBINE_TC
-      } else {
-        e = cudaMemcpyAsync(coef_, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
-        const float* ch = reinterpret_cast<const float*>(coef_);
-        const float* cl = ch + 2 * m;
-        block_combine32_kernel<<<grid_for(n_ * pw), kThreads, 0, s>>>(W, out, pw, bh, bl, X1, p1, ch, cl,
-                                                                       X2 ? X2 : X1, p2, ch + m, cl + m, L_, n_);
+      switch (KS * 8 + NT) {
+        case 9: MCD_COMBINE_TC(1, 1); break;
+        case 10: MCD_COMBINE_TC(1, 2); break;
+        case 11: MCD_COMBINE_TC(1, 3); break;
+        case 12: MCD_COMBINE_TC(1, 4); break;
+        case 17: MCD_COMBINE_TC(2, 1); break;
+        case 18: MCD_COMBINE_TC(2, 2); break;
+        case 19: MCD_COMBINE_TC(2, 3); break;
+        case 20: MCD_COMBINE_TC(2, 4); break;
+        case 25: MCD_COMBINE_TC(3, 1); break;
+        case 26: MCD_COMBINE_TC(3, 2); break;
+        case 27: MCD_COMBINE_TC(3, 3); break;
+        case 28: MCD_COMBINE_TC(3, 4); break;
+        case 33: MCD_COMBINE_TC(4, 1); break;
+        case 34: MCD_COMBINE_TC(4, 2); break;
+        case 35: MCD_COMBINE_TC(4, 3); break;
+        default: MCD_COMBINE_TC(4, 4); break;
       }
+#undef MCD_COMBINE_TC
     } else {
       e = cudaMemcpyAsync(coef_, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) return cuda_fail(c_, e, "block coefficients");
